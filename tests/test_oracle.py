@@ -1,0 +1,296 @@
+"""Pins for the CPU oracle, independent of the oracle itself.
+
+Each check is something the paper or mathematics fixes: exhaustive brute force
+over every injective map (Defs. 2-3), closed-form embedding counts, counts from
+a library routine (numpy matrix powers), a published hash's reference
+implementation (scikit-learn's MurmurHash3), the necessary-condition property
+of the Sec. III-A signature filter, and the composition of Alg. 3 join
+iterations into the full result.
+"""
+import itertools
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import helpers as H
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def og(g):
+    return oracle.OracleGraph(g.vlab, g.src, g.dst, g.elab)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("block", range(12))
+def test_backtracking_equals_bruteforce(block):
+    """Defs. 2-3: the backtracking enumerator equals exhaustive search (1200 cases)."""
+    rng = np.random.default_rng(1000 + block)
+    for case in range(100):
+        n = int(rng.integers(3, 10))
+        g = H.random_graph(rng, n, float(rng.uniform(0.2, 0.8)), int(rng.integers(1, 4)), int(rng.integers(1, 4)))
+        k = int(rng.integers(1, min(5, n) + 1))
+        if case % 2 == 0 and g.m > 0:
+            q = H.extracted_query(rng, g, k) or H.random_connected_query(rng, k, int(rng.integers(0, 3)), 3, 3)
+        else:
+            q = H.random_connected_query(rng, k, int(rng.integers(0, 3)), int(rng.integers(1, 4)),
+                                         int(rng.integers(1, 4)))
+        G = og(g)
+        got = oracle.enumerate_rows(G, q)
+        want = oracle.bruteforce_rows(G, q)
+        assert got.shape == want.shape and np.array_equal(got, want), (block, case)
+        c, fp = oracle.count(G, q, nthreads=3)
+        assert c == want.shape[0]
+        assert fp == oracle.fingerprint(want)
+
+
+def test_bruteforce_disconnected_query():
+    """The oracle also evaluates a disconnected query (two disjoint edges)."""
+    rng = np.random.default_rng(7)
+    for _ in range(30):
+        g = H.random_graph(rng, 7, 0.5, 2, 2)
+        q = H.query(4, [(0, 1), (2, 3)], rng.integers(0, 2, 4), rng.integers(0, 2, 2))
+        G = og(g)
+        assert np.array_equal(oracle.enumerate_rows(G, q), oracle.bruteforce_rows(G, q))
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n,k", [(5, 1), (5, 3), (6, 4), (7, 5), (8, 3), (9, 4)])
+def test_clique_in_complete_graph(n, k):
+    """Unlabelled k-clique in K_n: n!/(n-k)! embeddings."""
+    c, _ = oracle.count(og(H.complete(n)), H.clique_query(k))
+    assert c == math.perm(n, k)
+
+
+@pytest.mark.parametrize("n,k", [(6, 3), (7, 4), (9, 5)])
+def test_any_query_in_complete_graph(n, k):
+    """Any unlabelled k-vertex query in K_n: n!/(n-k)! (every injective map works)."""
+    for q in (H.path_query(k), H.star_query(k - 1)):
+        c, _ = oracle.count(og(H.complete(n)), q)
+        assert c == math.perm(n, k)
+
+
+@pytest.mark.parametrize("n", [4, 5, 9, 20])
+def test_triangle_in_cycle_is_zero(n):
+    c, _ = oracle.count(og(H.cycle(n)), H.clique_query(3))
+    assert c == 0
+
+
+@pytest.mark.parametrize("n,k", [(5, 2), (6, 4), (10, 6), (12, 12)])
+def test_path_in_cycle(n, k):
+    """P_k in C_n (n >= k >= 2): 2n embeddings."""
+    c, _ = oracle.count(og(H.cycle(n)), H.path_query(k))
+    assert c == 2 * n
+
+
+def test_edge_count_and_stars():
+    """Single edge: 2|E|; star K_{1,s}: sum_v deg(v)!/(deg(v)-s)!."""
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        g = H.random_graph(rng, 30, 0.2, 1, 1)
+        deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n)
+        G = og(g)
+        assert oracle.count(G, H.path_query(2))[0] == 2 * g.m
+        for s in (2, 3, 4):
+            assert oracle.count(G, H.star_query(s))[0] == sum(H.falling(int(d), s) for d in deg)
+
+
+def test_labelled_star():
+    """Labelled star: sum over centres of prod over (edge label, leaf label) keys of falling factorials."""
+    rng = np.random.default_rng(11)
+    for _ in range(10):
+        g = H.random_graph(rng, 40, 0.3, 3, 2)
+        G = og(g)
+        s = int(rng.integers(1, 5))
+        cl = int(rng.integers(0, 3))
+        leaf_vl = rng.integers(0, 3, s)
+        leaf_el = rng.integers(0, 2, s)
+        q = H.star_query(s, [cl] + list(leaf_vl), leaf_el)
+        need = {}
+        for a, b in zip(leaf_el, leaf_vl):
+            need[(int(a), int(b))] = need.get((int(a), int(b)), 0) + 1
+        nbrs = {v: [] for v in range(g.n)}
+        for a, b, l in zip(g.src, g.dst, g.elab):
+            nbrs[int(a)].append((int(l), int(g.vlab[b])))
+            nbrs[int(b)].append((int(l), int(g.vlab[a])))
+        want = 0
+        for v in range(g.n):
+            if g.vlab[v] != cl:
+                continue
+            prod = 1
+            for key, mk in need.items():
+                prod *= H.falling(sum(1 for x in nbrs[v] if x == key), mk)
+            want += prod
+        assert oracle.count(G, q)[0] == want
+
+
+def test_triangles_match_matrix_trace():
+    """Unlabelled triangle embeddings = trace(A^3) (numpy matrix product)."""
+    rng = np.random.default_rng(5)
+    for _ in range(8):
+        g = H.random_graph(rng, 25, float(rng.uniform(0.1, 0.5)), 1, 1)
+        A = np.zeros((g.n, g.n), np.int64)
+        A[g.src, g.dst] = 1
+        A[g.dst, g.src] = 1
+        assert oracle.count(og(g), H.clique_query(3))[0] == int(np.trace(A @ A @ A))
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 4), (5, 3)])
+def test_four_cycle_in_complete_bipartite(a, b):
+    """C4 in K_{a,b}: 2 a(a-1) b(b-1)."""
+    q = H.query(4, [(0, 1), (1, 2), (2, 3), (0, 3)])
+    assert oracle.count(og(H.complete_bipartite(a, b)), q)[0] == 2 * a * (a - 1) * b * (b - 1)
+
+
+def test_labels_select():
+    """A vertex-label mismatch or an edge-label mismatch removes the embedding."""
+    g = H.graph(3, [(0, 1), (1, 2)], vlab=[0, 1, 0], elab=[5, 6])
+    G = og(g)
+    assert oracle.count(G, H.query(2, [(0, 1)], [0, 1], [5]))[0] == 1
+    assert oracle.count(G, H.query(2, [(0, 1)], [0, 1], [6]))[0] == 1
+    assert oracle.count(G, H.query(2, [(0, 1)], [0, 1], [7]))[0] == 0
+    assert oracle.count(G, H.query(2, [(0, 1)], [1, 1], [5]))[0] == 0
+
+
+def test_non_induced():
+    """Matches are not induced: a path query matches inside a triangle (6 ways)."""
+    assert oracle.count(og(H.complete(3)), H.path_query(3))[0] == 6
+
+
+# ------------------------------------------------------------------ signature
+def test_murmur3_matches_library():
+    """The oracle's hash is MurmurHash3 x86_32: compare with scikit-learn's implementation."""
+    sk = pytest.importorskip("sklearn.utils")
+    rng = np.random.default_rng(9)
+    for _ in range(300):
+        a, b = (int(x) for x in rng.integers(-2**31, 2**31, 2))
+        key = struct.pack("<ii", a, b)
+        seed = int(rng.integers(0, 2**32))
+        assert oracle.murmur3_32(key, seed) == sk.murmurhash3_32(key, seed=seed, positive=True)
+    for ln in range(0, 13):
+        data = bytes(rng.integers(0, 256, ln).astype(np.uint8))
+        assert oracle.murmur3_32(data, 0x9747B28C) == sk.murmurhash3_32(data, seed=0x9747B28C, positive=True)
+
+
+def _group(el, nl):
+    return oracle.murmur3_32(struct.pack("<ii", el, nl), 0x9747B28C) % 240
+
+
+def test_signature_states():
+    """Sec. III-A: label stored in the first 32 bits; group states 00/01/11 for 0/1/>=2 pairs."""
+    # centre 0 (label 9): neighbours 1, 2 share key (edge 3, label 4); neighbour 3 has key (edge 1, label 2)
+    g = H.graph(4, [(0, 1), (0, 2), (0, 3)], vlab=[9, 4, 4, 2], elab=[3, 3, 1])
+    sig = oracle.data_signatures(og(g))
+    s0 = sig[0]
+    assert s0[0] == 9
+    g1, g2 = _group(3, 4), _group(1, 2)
+    bits = np.unpackbits(s0[1:].view(np.uint8), bitorder="little")
+    assert bits[2 * g1] == 1 and bits[2 * g1 + 1] == 1
+    if g2 != g1:
+        assert bits[2 * g2] == 1 and bits[2 * g2 + 1] == 0
+    assert bits.sum() == (2 if g1 == g2 else 3)
+    # a leaf: one pair (3, 9)
+    s1 = np.unpackbits(sig[1][1:].view(np.uint8), bitorder="little")
+    assert sig[1][0] == 4 and s1.sum() == 1 and s1[2 * _group(3, 9)] == 1
+
+
+def test_isolated_vertex_signature():
+    g = H.graph(3, [(0, 1)], vlab=[1, 2, 7], elab=[0])
+    sig = oracle.data_signatures(og(g))
+    assert sig[2][0] == 7 and not sig[2][1:].any()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_filter_is_sound(seed):
+    """Sec. III-A: every data vertex used at u by some embedding passes the filter for u."""
+    rng = np.random.default_rng(200 + seed)
+    for _ in range(25):
+        g = H.random_graph(rng, 12, 0.4, 2, 2)
+        G = og(g)
+        q = H.extracted_query(rng, g, int(rng.integers(2, 6)))
+        if q is None:
+            continue
+        rows = oracle.enumerate_rows(G, q)
+        member, counts = oracle.filter_sets(G, q)
+        assert np.array_equal(counts, member.sum(axis=1))
+        for u in range(q.k):
+            assert member[u, rows[:, u]].all()
+            # the label part is exact equality
+            assert not member[u, g.vlab != q.vlab[u]].any()
+
+
+def test_filter_prunes_by_neighbourhood():
+    """A vertex with the right label but too few matching neighbours is pruned."""
+    # data: 0 - 1 (labels 0,1), query: centre label 0 with two leaves labelled 1 (same key twice -> state 11)
+    g = H.graph(3, [(0, 1), (0, 2)], vlab=[0, 1, 2], elab=[0, 0])
+    q = H.star_query(2, [0, 1, 1], [0, 0])
+    member, _ = oracle.filter_sets(og(g), q)
+    assert not member[0, 0]
+
+
+# ------------------------------------------------------------------ join step
+@pytest.mark.parametrize("seed", range(6))
+def test_join_steps_compose_to_full_result(seed):
+    """Alg. 2/3: seeding M with C(u_first) and applying one join per vertex yields every embedding."""
+    rng = np.random.default_rng(300 + seed)
+    for _ in range(15):
+        g = H.random_graph(rng, 14, 0.35, 2, 2)
+        G = og(g)
+        q = H.extracted_query(rng, g, int(rng.integers(2, 6)))
+        if q is None:
+            continue
+        want = oracle.enumerate_rows(G, q)
+        member, _ = oracle.filter_sets(G, q)
+        qadj = {}
+        for a, b, l in zip(q.src, q.dst, q.elab):
+            qadj[(int(a), int(b))] = qadj[(int(b), int(a))] = int(l)
+        # any connected order: random BFS-like growth
+        order = [int(rng.integers(0, q.k))]
+        while len(order) < q.k:
+            cand = sorted({b for (a, b) in qadj if a in order and b not in order})
+            order.append(int(rng.choice(cand)))
+        for use_filter in (True, False):
+            M = np.nonzero(member[order[0]] if use_filter else g.vlab == q.vlab[order[0]])[0].astype(np.int32)[:, None]
+            for t in range(1, q.k):
+                u = order[t]
+                cols = [c for c in range(t) if (order[c], u) in qadj]
+                labs = [qadj[(order[c], u)] for c in cols]
+                inC = member[u] if use_filter else (g.vlab == q.vlab[u])
+                M = oracle.join_step(G, M, inC, cols, labs)
+            # back to query-vertex order
+            if M.shape[0]:
+                out = np.empty_like(M)
+                out[:, order] = M
+            else:
+                out = np.empty((0, q.k), np.int32)
+            assert np.array_equal(oracle.sort_rows(out), want)
+
+
+def test_join_step_rules():
+    """One step: injectivity (set subtraction), candidate set and every linking edge apply."""
+    # triangle 0-1-2 plus pendant 2-3; all labels 0
+    g = H.graph(4, [(0, 1), (1, 2), (0, 2), (2, 3)])
+    G = og(g)
+    M = np.array([[0, 1], [1, 0], [2, 3]], np.int32)
+    everyone = np.ones(4, bool)
+    # extend by a vertex adjacent to column 0 only
+    got = oracle.join_step(G, M, everyone, [0], [0])
+    assert [tuple(r) for r in got] == [(0, 1, 2), (1, 0, 2), (2, 3, 0), (2, 3, 1)]
+    # adjacent to both columns
+    got = oracle.join_step(G, M, everyone, [0, 1], [0, 0])
+    assert [tuple(r) for r in got] == [(0, 1, 2), (1, 0, 2)]
+    # candidate set excludes vertex 2
+    inC = np.array([1, 1, 0, 1], bool)
+    assert oracle.join_step(G, M, inC, [0, 1], [0, 0]).shape[0] == 0
+
+
+def test_fingerprint_is_order_independent():
+    rng = np.random.default_rng(1)
+    rows = rng.integers(0, 1000, (500, 6)).astype(np.int32)
+    fp = oracle.fingerprint(rows)
+    assert fp == oracle.fingerprint(rows[rng.permutation(500)])
+    assert fp != oracle.fingerprint(rows[:-1])
+    assert fp[0] == 500
