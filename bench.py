@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark: embeddings/s of the GB300 subgraph-isomorphism path.
+
+One step = every query of the workload (signature filter, seed, and one join
+iteration per remaining query vertex), with the data graph resident in HBM.
+Default workload: R-MAT 2^20 vertices / 16M undirected edges, 64 Zipf(1.1)
+vertex labels, 8 uniform edge labels, 100 random-walk queries with 6-12
+vertices (half sparse, half dense), all embeddings materialised on the device.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead
+(the slow plain program the GPU path is checked against), on a bounded sample.
+Multi-GPU (torchrun): queries are sharded round-robin over ranks; the graph
+is replicated; there is no data-path collective ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "embeddings/s & queries/s on 1 GB300; served p50/p99 vs plain per-query GPU path"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2: written between timed steps
+
+
+def _threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def parse_query_list(spec: str, n: int) -> list[int]:
+    """'3,5,8' or 'a:b' -> query indices (a subset, for small profiling runs)."""
+    if ":" in spec:
+        a, b = spec.split(":")
+        return list(range(int(a or 0), min(int(b or n), n)))
+    return [int(x) for x in spec.split(",") if x.strip()]
+
+
+def cpu_sample(queries, n: int = 8, max_bound: float = 2e7) -> list[int]:
+    """Deterministic CPU sample: the first n queries whose admission bound is <= max_bound."""
+    idx = [i for i, q in enumerate(queries) if q.bound <= max_bound]
+    return idx[:n]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("join.cu", "common.cuh", "scan.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1906_03420_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """ncu DRAM bytes per k_join launch recorded under profiles/, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_join_{workload}_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1906_03420_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    pkg.load()
+    w = synth.WORKLOADS[args.workload]
+    g = synth.workload_graph(args.workload)
+    queries = synth.queries(args.workload)
+    if args.queries:
+        queries = [queries[i] for i in parse_query_list(args.queries, len(queries))]
+    mine = queries[rank::world]
+    G = pkg.Graph.from_synth(g, device=local_rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    row_cap = w.row_cap
+
+    def one_step(stats_list=None):
+        total = 0
+        for q in mine:
+            st = pkg.c_stats() if stats_list is not None else None
+            r = G.query(q, stream=stream, row_cap=row_cap, stats=st)
+            total += r.count
+            r.close()
+            if st is not None:
+                stats_list.append(st)
+        return total
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    step_ms = []
+    stats = []
+    embeddings = 0
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                               # L2 flush, outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        embeddings += one_step(stats)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+
+    dev_ms = sum(step_ms)
+    join_ms = sum(s.join_ms for s in stats)
+    join_bytes = sum(s.join_bytes for s in stats)
+    join_launches = sum(s.join_launches for s in stats)
+    filter_ms = sum(s.filter_ms for s in stats)
+    filter_bytes = sum(s.filter_bytes for s in stats)
+    kernels = sum(s.kernels for s in stats)
+    local = torch.tensor([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
+                          float(join_launches), filter_ms, float(filter_bytes), float(kernels)], dtype=torch.float64,
+                         device="cuda")
+    if world > 1:
+        gathered = [torch.zeros_like(local) for _ in range(world)]
+        dist.all_gather(gathered, local)
+        allv = torch.stack(gathered).cpu().numpy()
+    else:
+        allv = local.cpu().numpy()[None, :]
+    t_max_ms = float(allv[:, 0].max())
+    tot_emb = float(allv[:, 1].sum())
+    tot_q = float(allv[:, 2].sum())
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        import torch as _t
+        counts = []
+        for q in mine:
+            r = G.query(q, stream=stream, row_cap=row_cap, count_only=True)
+            counts.append((r.count, q.k))
+            r.close()
+        max_bytes = max([min(c, row_cap or c) * k * 4 for c, k in counts] + [4])
+        host = _t.empty(max_bytes // 4 + 1, dtype=_t.int32, pin_memory=True)
+        h2d = sum(q.vlab.nbytes + q.src.nbytes + q.dst.nbytes + q.elab.nbytes for q in mine)
+        d2h = 0
+        emb = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for q in mine:
+                r = G.query(q, stream=stream, row_cap=row_cap)
+                c = r.count
+                rows, _capped = r.copy_to(host.data_ptr(), c)
+                d2h += rows * q.k * 4 + 8
+                emb += c
+                r.close()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": emb / el if el > 0 else None, "unit": "embeddings/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // args.e2e_steps),
+               "steps": args.e2e_steps, "ms_per_step": el * 1e3 / args.e2e_steps,
+               "queries_per_s": len(mine) * args.e2e_steps / el if el > 0 else None}
+
+    if rank != 0:
+        return None
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    jb, jms, jl = float(allv[:, 4].sum()), float(allv[:, 3].sum()), float(allv[:, 5].sum())
+    achieved = (jb / jl) / ((jms / jl) * 1e-3) / 1e9 if jl > 0 and jms > 0 else None
+    roofline = {"bound": "hbm", "kernel": "k_join", "achieved": achieved,
+                "peak": hbm_peak if hbm_peak else 6800.0, "unit": "GB/s",
+                "peak_source": "measured" if hbm_peak else "fallback",
+                "frac": (achieved / (hbm_peak or 6800.0)) if achieved else None,
+                "traffic": recorded_traffic(args.workload),
+                "alg_bytes_per_launch": jb / jl if jl else None, "launches": int(jl),
+                "avg_launch_us": jms / jl * 1e3 if jl else None,
+                "share_of_device_time": jms / (t_max_ms * world) if t_max_ms else None}
+    fb, fms = float(allv[:, 7].sum()), float(allv[:, 6].sum())
+    cfg = {"workload": args.workload, "graph": w.graph.kind + f" n={w.graph.n} m={w.graph.m}",
+           "query_subset": args.queries or "all", "vertex_labels": w.graph.n_vlabels, "edge_labels": w.graph.n_elabels,
+           "queries": w.n_queries, "k_range": [w.k_lo, w.k_hi], "query_admission_bound": w.max_bound,
+           "row_cap": w.row_cap, "l2": "flushed between timed steps (512 MB write)",
+           "materialised": True, "parallelism": f"queries sharded over {world} GPU(s)"}
+    out = {"metric": METRIC, "value": tot_emb / (t_max_ms * 1e-3) if t_max_ms > 0 else None,
+           "unit": "embeddings/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t_max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded R-MAT graph, random-walk queries)",
+           "config": cfg, "queries_per_s": tot_q / (t_max_ms * 1e-3) if t_max_ms > 0 else None,
+           "embeddings_per_step": tot_emb / args.steps, "wall_s": wall, "roofline": roofline,
+           "filter": {"achieved_gbs": fb / (fms * 1e-3) / 1e9 if fms > 0 else None, "ms_per_step": fms / args.steps},
+           "gpu_launches": int(allv[:, 8].sum()), "clocks": clocks, "e2e": e2e}
+    if args.cpu_baseline and rank == 0:
+        out["cpu_baseline"] = cpu_baseline(queries, g)
+    return out
+
+
+def cpu_baseline(queries, g) -> dict:
+    import oracle
+    O = oracle.OracleGraph.from_synth(g)
+    idx = cpu_sample(queries)
+    emb = 0
+    t0 = time.perf_counter()
+    for i in idx:
+        emb += oracle.count(O, queries[i])[0]
+    el = time.perf_counter() - t0
+    return {"value": emb / el if el > 0 else None, "unit": "embeddings/s", "cores": _threads(), "kind": "oracle",
+            "sample": f"queries {idx} of the workload (first 8 with admission bound <= 2e7), "
+                      f"{emb} embeddings enumerated in {el:.1f} s"}
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args) -> dict:
+    import oracle
+    import synth
+
+    w = synth.WORKLOADS[args.workload]
+    g = synth.workload_graph(args.workload)
+    queries = synth.queries(args.workload)
+    O = oracle.OracleGraph.from_synth(g)
+    idx = cpu_sample(queries)
+    sample = [queries[i] for i in idx]
+
+    def step():
+        return sum(oracle.count(O, q)[0] for q in sample)
+
+    for _ in range(args.warmup):
+        step()
+    times, emb = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        emb += step()
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    value = emb / el if el > 0 else None
+    cfg = {"workload": args.workload, "graph": w.graph.kind + f" n={w.graph.n} m={w.graph.m}",
+           "queries": w.n_queries, "k_range": [w.k_lo, w.k_hi], "query_admission_bound": w.max_bound,
+           "materialised": False, "sample": idx}
+    desc = f"queries {idx} (first 8 with admission bound <= 2e7) per step, count + fingerprint enumeration"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "embeddings/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded R-MAT graph, random-walk queries)", "config": cfg,
+            "queries_per_s": len(sample) * args.steps / el if el > 0 else None,
+            "cpu_baseline": {"value": value, "unit": "embeddings/s", "cores": _threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "embeddings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsi", choices=["gsi", "reference"])
+    ap.add_argument("--workload", default="medium")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--queries", default="", help="subset of query indices ('3,5,8' or 'a:b'); default all")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * gsi.h -- C ABI of the GB300 (sm_103a) subgraph-isomorphism library.
+ *
+ * The library computes what Sun et al., "GSI: GPU-friendly Subgraph
+ * Isomorphism" (arXiv 1906.03420) defines: all matches of a labelled query
+ * graph Q in a labelled data graph G (Defs. 1-3, Sec. II-A), reported as
+ * mappings f: V(Q) -> V(G) that are injective, keep vertex labels and map
+ * every query edge to a data edge with the same label.  It follows the
+ * paper's two phases: signature filtering (Sec. III-A) and one vertex-oriented
+ * join iteration per query vertex (Algs. 2-4, Sec. V).
+ *
+ * Conventions for every call:
+ *   - Ids and labels are int32; counts are uint64.  Graphs are undirected and
+ *     simple: one edge (and one label) per unordered vertex pair, no loops.
+ *   - Input arrays are read during the call and copied; the caller keeps them.
+ *   - Objects (gsi_graph, gsi_result, gsi_server) are owned by the library
+ *     until the matching *_destroy call.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.  Calls return after their results are
+ *     ready unless stated otherwise.
+ *   - No call throws.  Failures return a status; gsi_last_error() then holds a
+ *     message for the calling thread.
+ *   - All device work runs in this library's own CUDA kernels for sm_103a;
+ *     there is no CPU fallback.  A missing or unusable GPU yields GSI_ECUDA.
+ */
+#ifndef GSI_H
+#define GSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSI_OK = 0,
+    GSI_EINVAL = 1,      /* invalid argument: id out of range, self-loop, duplicate
+                            edge, disconnected or empty query, k > 32, ... */
+    GSI_ENOMEM = 2,      /* the memory budget cannot hold even a one-row tile */
+    GSI_ECAPPED = 3,     /* gsi_result_copy: rows were truncated at the row cap;
+                            the count stays exact */
+    GSI_ETIMEOUT = 4,    /* a wait ran past its limit */
+    GSI_ECANCELLED = 5,  /* a served request was cancelled */
+    GSI_ECUDA = 6,       /* a CUDA call or kernel failed */
+    GSI_EBUSY = 7        /* a served request is not finished yet */
+} gsi_status;
+
+typedef struct gsi_graph gsi_graph;
+typedef struct gsi_result gsi_result;
+typedef struct gsi_server gsi_server;
+
+/* Largest query handled (query vertices are tracked in 32-bit masks). */
+#define GSI_MAX_QUERY_VERTICES 32
+
+/* Signature geometry (Sec. III-A): N = 512 bits per vertex; the first K = 32
+   bits hold the vertex label; the other 480 bits are 240 two-bit groups. */
+#define GSI_SIG_WORDS 16
+#define GSI_SIG_GROUPS 240
+
+/* ------------------------------------------------------------------ graph */
+typedef struct {
+    int32_t device;      /* CUDA device ordinal */
+    void *stream;        /* stream for the build */
+} gsi_graph_opts;
+
+typedef struct {
+    int32_t n;           /* |V(G)| */
+    int32_t n_elabels;   /* L: edge labels are 0..L-1 */
+    int64_t m;           /* |E(G)| (undirected) */
+    uint64_t device_bytes;   /* bytes held on the device by the graph */
+    double build_ms;         /* device time of the build */
+    /* device pointers, valid until gsi_graph_destroy (read-only):
+       off  uint32[n*L + 1]: N(v,l) = ci[off[v*L+l] .. off[v*L+l+1])
+       ci   int32[2m]: neighbour lists, ascending within each (v,l)
+       sig  uint32[16*n]: signature word w of vertex v at sig[w*n + v]
+            (column-first, Sec. III-A); word 0 is the vertex label */
+    const uint32_t *off;
+    const int32_t *ci;
+    const uint32_t *sig;
+} gsi_graph_info;
+
+/*
+ * Load G into device memory and build its label-partitioned CSR (the
+ * edge-label-partitioned graphs P(G,l) of Sec. IV in the "basic
+ * representation": one row-offset entry per (vertex, label)), the per-label
+ * edge frequencies freq(l) (Table "Notations") and the column-first signature
+ * table (Sec. III-A).
+ *   vlab  int32[n]   vertex labels (any int32)
+ *   src, dst, elab  int32[m]   edge i = {src[i], dst[i]} with label elab[i] >= 0
+ * Errors: GSI_EINVAL for n < 1, m < 0, an id outside [0,n), a self-loop, a
+ * negative edge label, 2m >= 2^32, or the same vertex pair given twice;
+ * GSI_ECUDA / GSI_ENOMEM for device failures.  *out is set only on GSI_OK.
+ */
+gsi_status gsi_graph_create(const int32_t *vlab, int32_t n, const int32_t *src, const int32_t *dst,
+                            const int32_t *elab, int64_t m, const gsi_graph_opts *opts, gsi_graph **out);
+void gsi_graph_destroy(gsi_graph *g);
+gsi_status gsi_graph_get_info(const gsi_graph *g, gsi_graph_info *info);
+/*
+ * Copy the built layout out (host or device destinations; any may be NULL):
+ * off uint32[n*L + 1], ci int32[2m], sig uint32[16*n] (column-first).
+ */
+gsi_status gsi_graph_export(const gsi_graph *g, uint32_t *off, int32_t *ci, uint32_t *sig);
+/* freq(l) for l in [0, L): number of undirected edges with label l. */
+gsi_status gsi_graph_label_freq(const gsi_graph *g, uint64_t *freq, int32_t max_labels);
+
+/* ------------------------------------------------------------------ query */
+typedef struct {
+    /* device time (CUDA events on the query's stream) and work, accumulated */
+    double filter_ms, join_ms, other_ms;
+    uint64_t filter_launches, join_launches, other_launches;
+    uint64_t filter_bytes;   /* algorithmic bytes of the filter */
+    uint64_t join_bytes;     /* algorithmic bytes of the join steps */
+    uint64_t join_items;     /* candidates examined: sum of |N(v'_i, l0)| */
+    uint64_t tiles;          /* row ranges processed (memory-bounded splits) */
+    uint64_t peak_bytes;     /* peak intermediate-table bytes */
+    uint64_t kernels;        /* kernels launched by this library */
+    uint64_t cand[GSI_MAX_QUERY_VERTICES];   /* |C(u)| per query vertex */
+    int32_t order[GSI_MAX_QUERY_VERTICES];   /* join order (query vertex ids) */
+    int32_t k;
+} gsi_stats;
+
+typedef enum { GSI_ISOMORPHISM = 0 } gsi_semantics;
+
+typedef struct {
+    void *stream;            /* stream for all device work of the query */
+    uint64_t row_cap;        /* max embeddings materialised; 0 = no cap.  The
+                                count stays exact beyond the cap. */
+    uint64_t mem_budget;     /* bytes for intermediate tables; 0 = half of the
+                                device's free memory at call time */
+    int32_t count_only;      /* 1: count embeddings, materialise none */
+    int32_t semantics;       /* GSI_ISOMORPHISM */
+    const int32_t *order;    /* optional join order (k query vertex ids, each
+                                connected to an earlier one); NULL = Alg. 2 */
+    gsi_stats *stats;        /* optional: timing and work counters */
+} gsi_query_opts;
+
+/*
+ * Find all embeddings of Q in G (Defs. 2-3): filter (Sec. III-A), order by
+ * Alg. 2, then one join iteration per remaining query vertex (Alg. 3 with the
+ * Alg. 4 upper bound on each row's output).
+ *   qvlab int32[k]; query edges {qsrc[i], qdst[i]} with label qelab[i], i < qm.
+ * Q must be connected (the paper assumes so, Sec. II-A), have 1 <= k <= 32
+ * vertices, no self-loop and no repeated vertex pair: otherwise GSI_EINVAL.
+ * opts may be NULL (defaults).  *out receives a result object on GSI_OK.
+ */
+gsi_status gsi_query_run(gsi_graph *g, const int32_t *qvlab, int32_t k, const int32_t *qsrc,
+                         const int32_t *qdst, const int32_t *qelab, int32_t qm, const gsi_query_opts *opts,
+                         gsi_result **out);
+
+/* Exact number of embeddings (also beyond the row cap). */
+gsi_status gsi_result_count(const gsi_result *r, uint64_t *count);
+/* Number of query vertices k (columns of each row). */
+gsi_status gsi_result_columns(const gsi_result *r, int32_t *k);
+/*
+ * Copy up to max_rows materialised embeddings into dst (host or device
+ * memory; the library detects which), row-major int32[rows][k], column j =
+ * query vertex j.  Row order is unspecified.  *rows receives the number
+ * copied.  Returns GSI_ECAPPED when fewer rows were materialised than the
+ * count (row cap or count-only), GSI_OK otherwise.
+ */
+gsi_status gsi_result_copy(const gsi_result *r, int32_t *dst, uint64_t max_rows, uint64_t *rows);
+void gsi_result_destroy(gsi_result *r);
+
+/* ------------------------------------------------------- step-level calls */
+/*
+ * Signature filter alone (Sec. III-A): for every query vertex u, the bitmap
+ * of C(u) = { v : L(v) = L(u) and S(v) & S(u) = S(u) } (n bits, bit v of word
+ * v/32) and |C(u)|.  bitmaps: uint32[k][ceil(n/32)], counts: uint64[k], both
+ * host or device memory.
+ */
+gsi_status gsi_filter(gsi_graph *g, const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
+                      const int32_t *qelab, int32_t qm, uint32_t *bitmaps, uint64_t *counts, void *stream);
+
+/* Query-vertex signatures (Sec. III-A), vertex-major uint32[k][16]. */
+gsi_status gsi_query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
+                                const int32_t *qelab, int32_t qm, uint32_t *sig);
+
+/*
+ * One join iteration (Alg. 3) on device buffers.  M: int32[R][t] row-major;
+ * cand: C(u) bitmap (uint32[ceil(n/32)]); linking edges (col[j], lab[j]) for
+ * j < d, with j = 0 the first edge e0 whose list bounds each row's output
+ * (Alg. 4).  Writes rows (m || w) to out (int32[out_cap][t+1]) and the number
+ * of rows found to *count (host).  Rows beyond out_cap are counted, not
+ * written.  Scratch memory is allocated stream-ordered on `stream`.
+ * Errors: GSI_EINVAL for t < 1, t >= 32, d < 1, d > t, a column outside
+ * [0,t) or a label < 0.
+ */
+gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, const uint32_t *cand,
+                         const int32_t *col, const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
+                         uint64_t *count, void *stream);
+
+/*
+ * Alg. 2's matching order (host only, no GPU): cand[u] = |C(u)|, freq[l] for
+ * l < n_labels.  order_out[k]: query vertex ids in join order; first_edge[k]:
+ * for position p >= 1, the earlier query vertex whose edge to order[p] has the
+ * least frequent label (Alg. 4), -1 at p = 0.
+ */
+gsi_status gsi_plan_order(int32_t k, const int32_t *qsrc, const int32_t *qdst, const int32_t *qelab, int32_t qm,
+                          const uint64_t *cand, const uint64_t *freq, int32_t n_labels, int32_t *order_out,
+                          int32_t *first_edge);
+
+/* --------------------------------------------------------------- batched */
+typedef struct {
+    const int32_t *vlab;     /* int32[k] */
+    int32_t k;
+    const int32_t *src, *dst, *elab;   /* int32[qm] */
+    int32_t qm;
+} gsi_query_desc;
+
+typedef struct {
+    void *stream;
+    uint64_t row_cap;        /* per query */
+    uint64_t mem_budget;     /* bytes for all intermediate tables of the batch */
+    int32_t count_only;
+    gsi_stats *stats;        /* optional, accumulated over the batch */
+} gsi_batch_opts;
+
+/*
+ * Run nq queries together (a shared work queue of (query, step, row-range)
+ * tiles).  outs[i] receives query i's result (or NULL if its status is not
+ * GSI_OK); statuses (optional, int32[nq]) receives per-query status.
+ */
+gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
+                         gsi_result **outs, int32_t *statuses);
+
+/* ---------------------------------------------------------------- served */
+typedef struct {
+    uint64_t mem_budget;     /* bytes for intermediate tables of admitted queries */
+    int32_t n_streams;       /* concurrent streams (slots) */
+    uint64_t row_cap;        /* per query */
+    int32_t count_only;
+} gsi_server_opts;
+
+/* A serving loop over a resident graph (continuous batching). */
+gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opts, gsi_server **out);
+/* Enqueue a query (copied).  *ticket identifies it in gsi_server_poll. */
+gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, uint64_t *ticket);
+/*
+ * Wait up to timeout_ms (0 = do not wait, < 0 = wait until done) for a ticket.
+ * GSI_OK: *out receives the result (ownership passes to the caller) and the
+ * ticket is retired.  GSI_EBUSY: not finished.  Other codes: the query failed.
+ * latency_ms (optional) receives submit-to-completion time.
+ */
+gsi_status gsi_server_poll(gsi_server *s, uint64_t ticket, int32_t timeout_ms, gsi_result **out,
+                           double *latency_ms);
+gsi_status gsi_server_cancel(gsi_server *s, uint64_t ticket);
+void gsi_server_destroy(gsi_server *s);
+
+/* ------------------------------------------------------------------ misc */
+/* Message of the calling thread's last failure ("" if none). */
+const char *gsi_last_error(void);
+/* Library version string. */
+const char *gsi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSI_H */

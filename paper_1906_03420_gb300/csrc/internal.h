@@ -1,0 +1,80 @@
+// Declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gsi.h"
+
+struct gsi_graph {
+    int device = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t L = 1;              // edge labels 0..L-1
+    int32_t nwords = 0;         // ceil(n / 32): words of one candidate bitmap
+    uint32_t *off = nullptr;    // [n*L + 1]
+    int32_t *ci = nullptr;      // [2m]
+    uint32_t *sig = nullptr;    // [16 * n], column-first
+    std::vector<uint64_t> freq; // [L]
+    uint64_t device_bytes = 0;
+    double build_ms = 0;
+};
+
+namespace gsi {
+
+// ------------------------------------------------------------------ sort
+// Ascending LSD radix sort of n keys over their low `bits` bits.  keys and
+// tmp hold n keys each; the result ends in keys.  Scratch is allocated
+// stream-ordered.
+gsi_status radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, cudaStream_t st);
+
+// ----------------------------------------------------------------- graph
+gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32_t *src, const int32_t *dst,
+                       const int32_t *elab, int64_t m, cudaStream_t st);
+
+// ---------------------------------------------------------------- filter
+struct QuerySig {
+    int32_t k = 0;
+    uint32_t sig[GSI_MAX_QUERY_VERTICES][GSI_SIG_WORDS];
+};
+void query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
+                      const int32_t *qelab, int32_t qm, QuerySig *out);
+// bitmaps: device uint32[k][nwords]; counts: device unsigned long long[k] (zeroed here).
+gsi_status launch_filter(const gsi_graph *g, const QuerySig &q, uint32_t *bitmaps, unsigned long long *counts,
+                         cudaStream_t st);
+// Compact the bitmap of C(u) into the int32 list out (ascending); scratch: uint32[scan_blocks+1].
+gsi_status launch_seed(const gsi_graph *g, const uint32_t *bitmap, int32_t *out, uint32_t *scratch,
+                       cudaStream_t st);
+int64_t seed_scratch_words(const gsi_graph *g);
+
+// ------------------------------------------------------------------ join
+struct JoinStep {
+    int32_t t = 0;                       // columns of M
+    int32_t d = 0;                       // linking edges; [0] is e0
+    int32_t col[GSI_MAX_QUERY_VERTICES];
+    int32_t lab[GSI_MAX_QUERY_VERTICES];
+    int32_t perm[GSI_MAX_QUERY_VERTICES + 1];   // output position of each column
+};
+
+constexpr int JOIN_NT = 256;
+constexpr int JOIN_VT = 4;
+constexpr int JOIN_NV = JOIN_NT * JOIN_VT;
+constexpr int JOIN_ROW_WEIGHT = 2;      // slots charged per row (row staging work)
+
+// Exclusive scan over rows of (|N(M[i][col0], lab0)| + W): F[0..R], F[R] = total slots.
+gsi_status launch_join_scan(const gsi_graph *g, const int32_t *M, uint64_t R, const JoinStep &s, uint64_t *F,
+                            uint64_t *scratch, cudaStream_t st);
+int64_t join_scan_scratch(uint64_t R);
+// part[b] = first row of slot tile b, for b in [0, join_tiles(total)]; total = F[R].
+gsi_status launch_partition(const uint64_t *F, uint64_t R, uint64_t total, int64_t *part, cudaStream_t st);
+// The fused join kernel.  out_count (device) is incremented by the number of
+// survivors; stats (device, nullable): [0] algorithmic bytes, [1] candidates.
+gsi_status launch_join(const gsi_graph *g, const int32_t *M, uint64_t R, const JoinStep &s, const uint64_t *F,
+                       uint64_t total, const int64_t *part, const uint32_t *cand, int32_t *out, uint64_t out_cap,
+                       unsigned long long *out_count, int count_only, unsigned long long *stats, cudaStream_t st);
+inline uint64_t join_tiles(uint64_t total) { return (total + JOIN_NV - 1) / JOIN_NV; }
+
+}  // namespace gsi

@@ -1,0 +1,513 @@
+// Host runtime behind the C ABI: graph objects, query validation, the Alg. 2
+// planner, the memory-bounded depth-first join driver and result objects.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "runtime.h"
+
+namespace gsi {
+
+static thread_local std::string t_last_error;
+void set_error(const std::string &msg) { t_last_error = msg; }
+const char *last_error() { return t_last_error.c_str(); }
+
+// --------------------------------------------------------------- devices
+static std::once_flag g_pool_once[64];
+
+gsi_status prepare_device(int dev) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        set_error("no CUDA device available");
+        return GSI_ECUDA;
+    }
+    if (dev < 0 || dev >= ndev) {
+        set_error("device ordinal out of range");
+        return GSI_EINVAL;
+    }
+    GSI_CUDA_TRY(cudaSetDevice(dev));
+    // a failed call of an earlier request leaves a non-sticky error behind;
+    // clear it so that launch checks below report only this request's errors
+    (void)cudaGetLastError();
+    if (dev < 64) {
+        std::call_once(g_pool_once[dev], [dev]() {
+            // keep freed stream-ordered blocks cached for reuse by later queries
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+        });
+    }
+    return GSI_OK;
+}
+
+// ------------------------------------------------------- query validation
+gsi_status validate_query(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
+                          const int32_t *qelab, int32_t qm, QueryGraph *q) {
+    if (k < 1 || k > GSI_MAX_QUERY_VERTICES) {
+        set_error("query: need 1 <= k <= 32");
+        return GSI_EINVAL;
+    }
+    if (qm < 0 || (qm > 0 && (!qsrc || !qdst || !qelab)) || !qvlab) {
+        set_error("query: null arrays or negative edge count");
+        return GSI_EINVAL;
+    }
+    q->k = k;
+    for (int u = 0; u < k; ++u) {
+        q->vlab[u] = qvlab[u];
+        for (int w = 0; w < k; ++w) q->elab[u][w] = -1;
+    }
+    for (int e = 0; e < qm; ++e) {
+        int a = qsrc[e], b = qdst[e];
+        if (a < 0 || a >= k || b < 0 || b >= k) {
+            set_error("query: vertex id out of range");
+            return GSI_EINVAL;
+        }
+        if (a == b) {
+            set_error("query: self-loop");
+            return GSI_EINVAL;
+        }
+        if (qelab[e] < 0) {
+            set_error("query: negative edge label");
+            return GSI_EINVAL;
+        }
+        if (q->elab[a][b] >= 0) {
+            set_error("query: vertex pair given twice");
+            return GSI_EINVAL;
+        }
+        q->elab[a][b] = q->elab[b][a] = qelab[e];
+    }
+    // connectivity (the paper assumes a connected query, Sec. II-A)
+    uint32_t seen = 1u, frontier = 1u;
+    while (frontier) {
+        uint32_t next = 0;
+        for (int u = 0; u < k; ++u)
+            if ((frontier >> u) & 1u)
+                for (int w = 0; w < k; ++w)
+                    if (q->elab[u][w] >= 0 && !((seen >> w) & 1u)) next |= 1u << w;
+        seen |= next;
+        frontier = next;
+    }
+    uint32_t all = k == 32 ? 0xffffffffu : ((1u << k) - 1u);
+    if (seen != all) {
+        set_error("query: not connected");
+        return GSI_EINVAL;
+    }
+    q->qm = qm;
+    q->src.assign(qsrc, qsrc + qm);
+    q->dst.assign(qdst, qdst + qm);
+    q->lab.assign(qelab, qelab + qm);
+    q->vl.assign(qvlab, qvlab + k);
+    return GSI_OK;
+}
+
+// --------------------------------------------------------------- planner
+// Alg. 2: score(u) = |C(u)| / deg(u); start at the minimum; then repeatedly
+// take the unmatched vertex of least score adjacent to the matched part, and
+// after each pick multiply its neighbours' scores by freq(label of the edge).
+// Alg. 4: the first edge e0 of each step is the linking edge of least
+// frequent label.  Ties: lowest query vertex id.
+void plan_order(const QueryGraph &q, const uint64_t *cand, const uint64_t *freq, int32_t nlabels, int32_t *order,
+                int32_t *first) {
+    const int k = q.k;
+    double score[GSI_MAX_QUERY_VERTICES];
+    auto fq = [&](int32_t l) -> double { return (l >= 0 && l < nlabels) ? (double)freq[l] : 0.0; };
+    for (int u = 0; u < k; ++u) {
+        int deg = 0;
+        for (int w = 0; w < k; ++w) deg += q.elab[u][w] >= 0;
+        score[u] = (double)cand[u] / (double)(deg > 0 ? deg : 1);
+    }
+    uint32_t matched = 0;
+    for (int p = 0; p < k; ++p) {
+        int best = -1;
+        for (int u = 0; u < k; ++u) {
+            if ((matched >> u) & 1u) continue;
+            if (p > 0) {
+                bool linked = false;
+                for (int w = 0; w < k; ++w) linked |= ((matched >> w) & 1u) && q.elab[u][w] >= 0;
+                if (!linked) continue;
+            }
+            if (best < 0 || score[u] < score[best]) best = u;
+        }
+        order[p] = best;
+        first[p] = -1;
+        if (p > 0) {
+            double bf = 0;
+            for (int w = 0; w < k; ++w) {
+                if (!((matched >> w) & 1u) || q.elab[best][w] < 0) continue;
+                double f = fq(q.elab[best][w]);
+                if (first[p] < 0 || f < bf) { first[p] = w; bf = f; }
+            }
+        }
+        matched |= 1u << best;
+        for (int w = 0; w < k; ++w)
+            if (q.elab[best][w] >= 0) score[w] *= fq(q.elab[best][w]);
+    }
+}
+
+// JoinStep for position p (t = p columns), given the order and e0 choice.
+void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, std::vector<JoinStep> &steps) {
+    const int k = q.k;
+    int pos[GSI_MAX_QUERY_VERTICES];
+    for (int p = 0; p < k; ++p) pos[order[p]] = p;
+    steps.assign(k, JoinStep());
+    for (int p = 1; p < k; ++p) {
+        JoinStep &s = steps[p];
+        s.t = p;
+        s.d = 0;
+        int u = order[p];
+        s.col[s.d] = pos[first[p]];
+        s.lab[s.d] = q.elab[u][first[p]];
+        ++s.d;
+        for (int c = 0; c < p; ++c) {
+            int w = order[c];
+            if (w == first[p] || q.elab[u][w] < 0) continue;
+            s.col[s.d] = c;
+            s.lab[s.d] = q.elab[u][w];
+            ++s.d;
+        }
+        for (int c = 0; c <= p; ++c) s.perm[c] = (p == k - 1) ? order[c] : c;
+    }
+}
+
+// -------------------------------------------------------------- timing
+void Timer::begin(int kind) {
+    if (!on) return;
+    Rec r;
+    r.kind = kind;
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+}
+void Timer::end() {
+    if (!on || recs.empty()) return;
+    cudaEventRecord(recs.back().b, st);
+}
+void Timer::resolve(gsi_stats *s) {
+    for (auto &r : recs) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (s) {
+            if (r.kind == 0) { s->filter_ms += ms; s->filter_launches++; }
+            else if (r.kind == 1) { s->join_ms += ms; s->join_launches++; }
+            else { s->other_ms += ms; s->other_launches++; }
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    recs.clear();
+}
+
+// ----------------------------------------------------------------- driver
+static gsi_status dalloc(Exec &x, void **p, uint64_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, x.st);
+    if (e != cudaSuccess) {
+        set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return GSI_ENOMEM;
+    }
+    return GSI_OK;
+}
+
+static gsi_status read_u64(Exec &x, const void *dptr, uint64_t *val) {
+    GSI_CUDA_TRY(cudaMemcpyAsync(x.h_pinned, dptr, 8, cudaMemcpyDeviceToHost, x.st));
+    GSI_CUDA_TRY(cudaStreamSynchronize(x.st));
+    *val = x.h_pinned[0];
+    return GSI_OK;
+}
+
+gsi_status Exec::add_chunk(int32_t *rows, uint64_t nrows, uint64_t alloc_rows) {
+    if (nrows == 0) {
+        cudaFreeAsync(rows, st);
+        return GSI_OK;
+    }
+    if (alloc_rows > 2 * nrows + 1024) {   // shrink a loose Prealloc bound
+        int32_t *tight = nullptr;
+        uint64_t bytes = nrows * (uint64_t)k * 4;
+        GSI_TRY(dalloc(*this, (void **)&tight, bytes));
+        GSI_CUDA_TRY(cudaMemcpyAsync(tight, rows, bytes, cudaMemcpyDeviceToDevice, st));
+        cudaFreeAsync(rows, st);
+        rows = tight;
+    }
+    res->chunks.push_back({rows, nrows});
+    res->materialised += nrows;
+    return GSI_OK;
+}
+
+// Extend the t-column table M (R rows) by position t, then recurse to the
+// last position.  Memory-bounded: when the step's buffers would exceed the
+// budget, M is halved by rows and each half is finished depth-first.
+gsi_status Exec::run(int t, const int32_t *M, uint64_t R) {
+    if (R == 0) return GSI_OK;
+    const JoinStep &s = steps[t];
+    const bool last = (t + 1 == k);
+    const uint64_t fbytes = 8 * (R + 1) + 8 * (uint64_t)join_scan_scratch(R);
+    auto split = [&]() -> gsi_status {
+        uint64_t h = R / 2;
+        GSI_TRY(run(t, M, h));
+        return run(t, M + h * (uint64_t)t, R - h);
+    };
+    if (live + fbytes > budget) {
+        if (R > 1) return split();
+        set_error("memory budget cannot hold a one-row tile");
+        return GSI_ENOMEM;
+    }
+    uint64_t *F = nullptr, *scr = nullptr;
+    GSI_TRY(dalloc(*this, (void **)&F, 8 * (R + 1)));
+    GSI_TRY(dalloc(*this, (void **)&scr, 8 * (uint64_t)join_scan_scratch(R)));
+    tm.begin(2);
+    gsi_status rc = launch_join_scan(g, M, R, s, F, scr, st);
+    tm.end();
+    kernels += 3;
+    uint64_t total = 0;
+    if (rc == GSI_OK) rc = read_u64(*this, F + R, &total);
+    cudaFreeAsync(scr, st);
+    if (rc != GSI_OK) {
+        cudaFreeAsync(F, st);
+        return rc;
+    }
+    const uint64_t sumcap = total - (uint64_t)JOIN_ROW_WEIGHT * R;
+    uint64_t out_rows = sumcap;
+    int count_mode = 0;
+    if (last) {
+        uint64_t room = row_cap ? (res->materialised >= row_cap ? 0 : row_cap - res->materialised) : sumcap;
+        out_rows = count_only ? 0 : std::min(sumcap, room);
+        count_mode = out_rows == 0;
+    }
+    const uint64_t ntiles = join_tiles(total);
+    const uint64_t obytes = out_rows * (uint64_t)(t + 1) * 4;
+    const uint64_t need = 8 * (R + 1) + 8 * (ntiles + 1) + obytes;
+    if (live + need > budget) {
+        cudaFreeAsync(F, st);
+        if (R > 1) return split();
+        set_error("memory budget cannot hold a one-row tile");
+        return GSI_ENOMEM;
+    }
+    int64_t *part = nullptr;
+    int32_t *out = nullptr;
+    rc = dalloc(*this, (void **)&part, 8 * (ntiles + 1));
+    if (rc == GSI_OK) rc = dalloc(*this, (void **)&out, obytes);
+    if (rc != GSI_OK) {
+        cudaFreeAsync(F, st);
+        if (part) cudaFreeAsync(part, st);
+        return rc;
+    }
+    live += need;
+    peak = std::max(peak, live);
+    ++tiles;
+    if (cudaMemsetAsync(d_scalars, 0, 8, st) != cudaSuccess) rc = GSI_ECUDA;
+    if (rc == GSI_OK) {
+        tm.begin(2);
+        rc = launch_partition(F, R, total, part, st);
+        tm.end();
+        kernels += total > 0;
+    }
+    if (rc == GSI_OK) {
+        tm.begin(1);
+        rc = launch_join(g, M, R, s, F, total, part, cand(s, t), out, out_rows, d_scalars, count_mode,
+                         stats ? d_scalars + 1 : nullptr, st);
+        tm.end();
+        kernels += total > 0;
+    }
+    uint64_t cnt = 0;
+    if (rc == GSI_OK) rc = read_u64(*this, d_scalars, &cnt);
+    cudaFreeAsync(F, st);
+    cudaFreeAsync(part, st);
+    live -= 8 * (R + 1) + 8 * (ntiles + 1);
+    if (rc != GSI_OK) {
+        cudaFreeAsync(out, st);
+        live -= obytes;
+        return rc;
+    }
+    if (last) {
+        res->count += cnt;
+        live -= obytes;
+        if (count_mode) {
+            cudaFreeAsync(out, st);
+            return GSI_OK;
+        }
+        return add_chunk(out, std::min(cnt, out_rows), out_rows);
+    }
+    rc = run(t + 1, out, cnt);
+    cudaFreeAsync(out, st);
+    live -= obytes;
+    return rc;
+}
+
+const uint32_t *Exec::cand(const JoinStep &s, int t) const {
+    (void)s;
+    return bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords;
+}
+
+gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o, gsi_result **out) {
+    GSI_TRY(prepare_device(g->device));
+    std::unique_ptr<gsi_result> res(new gsi_result());
+    res->k = q.k;
+    res->device = g->device;
+    Exec x;
+    x.g = g;
+    x.k = q.k;
+    x.st = (cudaStream_t)o.stream;
+    x.row_cap = o.row_cap;
+    x.count_only = o.count_only;
+    x.stats = o.stats;
+    x.res = res.get();
+    x.tm.on = o.stats != nullptr;
+    x.tm.st = x.st;
+    if (o.mem_budget) {
+        x.budget = o.mem_budget;
+    } else {
+        size_t fr = 0, totm = 0;
+        GSI_CUDA_TRY(cudaMemGetInfo(&fr, &totm));
+        x.budget = fr / 2;
+    }
+    // a query edge label that no data edge carries: no embeddings
+    for (int e = 0; e < q.qm; ++e)
+        if (q.lab[e] >= g->L || g->freq[q.lab[e]] == 0) {
+            *out = res.release();
+            return GSI_OK;
+        }
+    if (q.k > 1 && g->m == 0) {
+        *out = res.release();
+        return GSI_OK;
+    }
+
+    QuerySig qs;
+    query_signatures(q.vl.data(), q.k, q.src.data(), q.dst.data(), q.lab.data(), q.qm, &qs);
+    const uint64_t bm_words = (uint64_t)q.k * (uint64_t)g->nwords;
+    GSI_CUDA_TRY(cudaMallocHost(&x.h_pinned, 8 * (GSI_MAX_QUERY_VERTICES + 8)));
+    struct PinnedGuard {
+        Exec &x;
+        ~PinnedGuard() { cudaFreeHost(x.h_pinned); }
+    } pg{x};
+    unsigned long long *d_counts = nullptr;
+    GSI_TRY(dalloc(x, (void **)&x.bitmaps, bm_words * 4));
+    GSI_TRY(dalloc(x, (void **)&d_counts, 8 * GSI_MAX_QUERY_VERTICES + 32));
+    x.d_scalars = d_counts + GSI_MAX_QUERY_VERTICES;
+    GSI_CUDA_TRY(cudaMemsetAsync(x.d_scalars, 0, 32, x.st));
+
+    gsi_status rc = GSI_OK;
+    x.tm.begin(0);
+    rc = launch_filter(g, qs, x.bitmaps, d_counts, x.st);
+    x.tm.end();
+    x.kernels += 1;
+    uint64_t cand_h[GSI_MAX_QUERY_VERTICES] = {0};
+    if (rc == GSI_OK) {
+        if (cudaMemcpyAsync(x.h_pinned, d_counts, 8 * (size_t)q.k, cudaMemcpyDeviceToHost, x.st) != cudaSuccess ||
+            cudaStreamSynchronize(x.st) != cudaSuccess) {
+            set_error("filter: readback failed");
+            rc = GSI_ECUDA;
+        } else {
+            for (int u = 0; u < q.k; ++u) cand_h[u] = x.h_pinned[u];
+        }
+    }
+    bool empty = false;
+    for (int u = 0; u < q.k; ++u) empty |= cand_h[u] == 0;
+
+    int32_t order[GSI_MAX_QUERY_VERTICES], first[GSI_MAX_QUERY_VERTICES];
+    if (rc == GSI_OK && !empty) {
+        if (o.order) {
+            uint32_t seen = 0;
+            for (int p = 0; p < q.k && rc == GSI_OK; ++p) {
+                int u = o.order[p];
+                bool ok = u >= 0 && u < q.k && !((seen >> u) & 1u);
+                if (ok && p > 0) {
+                    bool linked = false;
+                    for (int w = 0; w < q.k; ++w) linked |= ((seen >> w) & 1u) && q.elab[u][w] >= 0;
+                    ok = linked;
+                }
+                if (!ok) {
+                    set_error("query: forced order is not a connected permutation");
+                    rc = GSI_EINVAL;
+                    break;
+                }
+                seen |= 1u << u;
+                order[p] = u;
+                first[p] = -1;
+                if (p > 0) {
+                    double bf = 0;
+                    for (int w = 0; w < q.k; ++w) {
+                        if (!((seen >> w) & 1u) || w == u || q.elab[u][w] < 0) continue;
+                        double f = (double)g->freq[q.elab[u][w]];
+                        if (first[p] < 0 || f < bf) { first[p] = w; bf = f; }
+                    }
+                }
+            }
+        } else {
+            plan_order(q, cand_h, g->freq.data(), g->L, order, first);
+        }
+    }
+    if (rc == GSI_OK && !empty) {
+        for (int p = 0; p < q.k; ++p) x.order[p] = order[p];
+        make_steps(q, order, first, x.steps);
+        // seed: M = C(u_first) as a one-column table (Alg. 2)
+        const uint64_t R0 = cand_h[order[0]];
+        int32_t *M0 = nullptr;
+        uint32_t *sscr = nullptr;
+        rc = dalloc(x, (void **)&M0, R0 * 4);
+        if (rc == GSI_OK) rc = dalloc(x, (void **)&sscr, 4 * (uint64_t)seed_scratch_words(g));
+        if (rc == GSI_OK) {
+            x.tm.begin(2);
+            rc = launch_seed(g, x.bitmaps + (uint64_t)order[0] * g->nwords, M0, sscr, x.st);
+            x.tm.end();
+            x.kernels += 3;
+        }
+        if (sscr) cudaFreeAsync(sscr, x.st);
+        if (rc == GSI_OK) {
+            x.live = R0 * 4;
+            x.peak = x.live;
+            if (q.k == 1) {
+                res->count = R0;
+                uint64_t keep = x.count_only ? 0 : (x.row_cap ? std::min(R0, x.row_cap) : R0);
+                if (keep) {
+                    rc = x.add_chunk(M0, keep, R0);
+                    M0 = nullptr;
+                }
+            } else {
+                rc = x.run(1, M0, R0);
+            }
+        }
+        if (M0) cudaFreeAsync(M0, x.st);
+    }
+    if (x.stats && rc == GSI_OK) {
+        // algorithmic bytes and candidates counted by the join kernels
+        if (cudaMemcpyAsync(x.h_pinned, x.d_scalars + 1, 16, cudaMemcpyDeviceToHost, x.st) == cudaSuccess &&
+            cudaStreamSynchronize(x.st) == cudaSuccess) {
+            x.join_bytes = x.h_pinned[0];
+            x.join_items = x.h_pinned[1];
+        }
+    }
+    cudaFreeAsync(x.bitmaps, x.st);
+    cudaFreeAsync(d_counts, x.st);
+    cudaError_t se = cudaStreamSynchronize(x.st);
+    if (rc == GSI_OK && se != cudaSuccess) {
+        set_error(std::string("query: ") + cudaGetErrorString(se));
+        rc = GSI_ECUDA;
+    }
+    if (x.stats) {
+        gsi_stats *s = x.stats;
+        x.tm.resolve(s);
+        s->k = q.k;
+        for (int u = 0; u < q.k; ++u) s->cand[u] = cand_h[u];
+        for (int p = 0; p < q.k; ++p) s->order[p] = (rc == GSI_OK && !empty) ? order[p] : -1;
+        s->tiles += x.tiles;
+        s->peak_bytes = std::max<uint64_t>(s->peak_bytes, x.peak);
+        s->filter_bytes += (uint64_t)g->n * (4 + 60) + bm_words * 4;
+        s->join_bytes += x.join_bytes;
+        s->join_items += x.join_items;
+        s->kernels += x.kernels;
+    }
+    if (rc != GSI_OK) return rc;
+    *out = res.release();
+    return GSI_OK;
+}
+
+}  // namespace gsi
+
+extern "C" const char *gsi_last_error(void) { return gsi::last_error(); }

@@ -1,0 +1,78 @@
+// Host-side runtime types shared by the C ABI translation units.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+struct gsi_result {
+    struct Chunk {
+        int32_t *rows;       // device, row-major [nrows][k], column j = query vertex j
+        uint64_t nrows;
+    };
+    int32_t k = 0;
+    int device = 0;
+    uint64_t count = 0;          // exact number of embeddings
+    uint64_t materialised = 0;   // rows held in chunks
+    std::vector<Chunk> chunks;
+    ~gsi_result();
+};
+
+namespace gsi {
+
+struct QueryGraph {
+    int32_t k = 0, qm = 0;
+    int32_t vlab[GSI_MAX_QUERY_VERTICES];
+    int32_t elab[GSI_MAX_QUERY_VERTICES][GSI_MAX_QUERY_VERTICES];   // -1 = no edge
+    std::vector<int32_t> src, dst, lab, vl;
+};
+
+struct Timer {
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;            // 0 filter, 1 join kernel, 2 other
+    };
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<Rec> recs;
+    void begin(int kind);
+    void end();
+    void resolve(gsi_stats *s);
+};
+
+// State of one query's execution (the depth-first join driver).
+struct Exec {
+    gsi_graph *g = nullptr;
+    cudaStream_t st = nullptr;
+    int k = 0;
+    int32_t order[GSI_MAX_QUERY_VERTICES];
+    std::vector<JoinStep> steps;     // steps[t] extends a t-column table
+    uint32_t *bitmaps = nullptr;     // [k][nwords], indexed by query vertex id
+    unsigned long long *d_scalars = nullptr;   // [0] step count, [1] bytes, [2] items
+    uint64_t *h_pinned = nullptr;
+    uint64_t budget = 0, live = 0, peak = 0, tiles = 0;
+    uint64_t row_cap = 0;
+    int count_only = 0;
+    uint64_t join_bytes = 0, join_items = 0;
+    uint64_t kernels = 0;            // kernels launched (scan = 3, partition, join, filter, seed = 3)
+    gsi_result *res = nullptr;
+    gsi_stats *stats = nullptr;
+    Timer tm;
+
+    gsi_status run(int t, const int32_t *M, uint64_t R);
+    gsi_status add_chunk(int32_t *rows, uint64_t nrows, uint64_t alloc_rows);
+    const uint32_t *cand(const JoinStep &s, int t) const;
+};
+
+gsi_status prepare_device(int dev);
+gsi_status validate_query(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
+                          const int32_t *qelab, int32_t qm, QueryGraph *q);
+void plan_order(const QueryGraph &q, const uint64_t *cand, const uint64_t *freq, int32_t nlabels, int32_t *order,
+                int32_t *first);
+void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, std::vector<JoinStep> &steps);
+gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o, gsi_result **out);
+
+}  // namespace gsi

@@ -1,0 +1,425 @@
+"""Thin ctypes binding of libgsi.so (include/gsi.h).
+
+Argument marshalling only: every step of the matching path runs in the
+library's CUDA kernels.  The library must be built (``_build.build()``); if it
+is missing or cannot load, importing raises -- there is no fallback.
+PyTorch is used for device buffers and streams (``torch.cuda`` tensors and
+``torch.cuda.Stream.cuda_stream`` handles).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+GSI_OK, GSI_EINVAL, GSI_ENOMEM, GSI_ECAPPED, GSI_ETIMEOUT, GSI_ECANCELLED, GSI_ECUDA, GSI_EBUSY = range(8)
+STATUS_NAMES = {0: "GSI_OK", 1: "GSI_EINVAL", 2: "GSI_ENOMEM", 3: "GSI_ECAPPED", 4: "GSI_ETIMEOUT",
+                5: "GSI_ECANCELLED", 6: "GSI_ECUDA", 7: "GSI_EBUSY"}
+MAX_QUERY_VERTICES = 32
+SIG_WORDS = 16
+
+EXPORTED = [
+    "gsi_graph_create", "gsi_graph_destroy", "gsi_graph_get_info", "gsi_graph_export", "gsi_graph_label_freq",
+    "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_destroy",
+    "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_plan_order",
+    "gsi_batch_run", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
+    "gsi_server_destroy", "gsi_last_error", "gsi_version",
+]
+
+
+class GsiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class c_graph_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class c_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_elabels", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("off", ctypes.c_void_p), ("ci", ctypes.c_void_p), ("sig", ctypes.c_void_p)]
+
+
+class c_stats(ctypes.Structure):
+    _fields_ = [("filter_ms", ctypes.c_double), ("join_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("filter_launches", ctypes.c_uint64), ("join_launches", ctypes.c_uint64),
+                ("other_launches", ctypes.c_uint64), ("filter_bytes", ctypes.c_uint64),
+                ("join_bytes", ctypes.c_uint64), ("join_items", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64), ("kernels", ctypes.c_uint64), ("cand", ctypes.c_uint64 * 32), ("order", ctypes.c_int32 * 32),
+                ("k", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("cand", "order")}
+        d["cand"] = list(self.cand)[: self.k]
+        d["order"] = list(self.order)[: self.k]
+        return d
+
+
+class c_query_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
+                ("count_only", ctypes.c_int32), ("semantics", ctypes.c_int32),
+                ("order", ctypes.POINTER(ctypes.c_int32)), ("stats", ctypes.POINTER(c_stats))]
+
+
+class c_query_desc(ctypes.Structure):
+    _fields_ = [("vlab", ctypes.POINTER(ctypes.c_int32)), ("k", ctypes.c_int32),
+                ("src", ctypes.POINTER(ctypes.c_int32)), ("dst", ctypes.POINTER(ctypes.c_int32)),
+                ("elab", ctypes.POINTER(ctypes.c_int32)), ("qm", ctypes.c_int32)]
+
+
+class c_batch_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
+                ("count_only", ctypes.c_int32), ("stats", ctypes.POINTER(c_stats))]
+
+
+class c_server_opts(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("n_streams", ctypes.c_int32), ("row_cap", ctypes.c_uint64),
+                ("count_only", ctypes.c_int32)]
+
+
+_lib = None
+I32P = ctypes.POINTER(ctypes.c_int32)
+U32P = ctypes.POINTER(ctypes.c_uint32)
+U64P = ctypes.POINTER(ctypes.c_uint64)
+VP = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libgsi.so; raises if it is absent (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"libgsi.so not built at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    st = ctypes.c_int
+    L.gsi_graph_create.argtypes = [I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int64,
+                                   ctypes.POINTER(c_graph_opts), ctypes.POINTER(VP)]
+    L.gsi_graph_create.restype = st
+    L.gsi_graph_destroy.argtypes = [VP]
+    L.gsi_graph_destroy.restype = None
+    L.gsi_graph_get_info.argtypes = [VP, ctypes.POINTER(c_graph_info)]
+    L.gsi_graph_get_info.restype = st
+    L.gsi_graph_export.argtypes = [VP, VP, VP, VP]
+    L.gsi_graph_export.restype = st
+    L.gsi_graph_label_freq.argtypes = [VP, U64P, ctypes.c_int32]
+    L.gsi_graph_label_freq.restype = st
+    L.gsi_query_run.argtypes = [VP, I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32,
+                                ctypes.POINTER(c_query_opts), ctypes.POINTER(VP)]
+    L.gsi_query_run.restype = st
+    L.gsi_result_count.argtypes = [VP, U64P]
+    L.gsi_result_count.restype = st
+    L.gsi_result_columns.argtypes = [VP, I32P]
+    L.gsi_result_columns.restype = st
+    L.gsi_result_copy.argtypes = [VP, VP, ctypes.c_uint64, U64P]
+    L.gsi_result_copy.restype = st
+    L.gsi_result_destroy.argtypes = [VP]
+    L.gsi_result_destroy.restype = None
+    L.gsi_filter.argtypes = [VP, I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, VP, VP, VP]
+    L.gsi_filter.restype = st
+    L.gsi_query_signatures.argtypes = [I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, U32P]
+    L.gsi_query_signatures.restype = st
+    L.gsi_join_step.argtypes = [VP, VP, ctypes.c_uint64, ctypes.c_int32, VP, I32P, I32P, ctypes.c_int32, VP,
+                                ctypes.c_uint64, U64P, VP]
+    L.gsi_join_step.restype = st
+    L.gsi_plan_order.argtypes = [ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, U64P, U64P, ctypes.c_int32,
+                                 I32P, I32P]
+    L.gsi_plan_order.restype = st
+    L.gsi_batch_run.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
+                                ctypes.POINTER(VP), I32P]
+    L.gsi_batch_run.restype = st
+    L.gsi_server_create.argtypes = [VP, ctypes.POINTER(c_server_opts), ctypes.POINTER(VP)]
+    L.gsi_server_create.restype = st
+    L.gsi_server_submit.argtypes = [VP, ctypes.POINTER(c_query_desc), U64P]
+    L.gsi_server_submit.restype = st
+    L.gsi_server_poll.argtypes = [VP, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(VP),
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.gsi_server_poll.restype = st
+    L.gsi_server_cancel.argtypes = [VP, ctypes.c_uint64]
+    L.gsi_server_cancel.restype = st
+    L.gsi_server_destroy.argtypes = [VP]
+    L.gsi_server_destroy.restype = None
+    L.gsi_last_error.argtypes = []
+    L.gsi_last_error.restype = ctypes.c_char_p
+    L.gsi_version.argtypes = []
+    L.gsi_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str, ok=(GSI_OK,)):
+    if rc not in ok:
+        msg = (_lib.gsi_last_error() or b"").decode()
+        raise GsiError(rc, f"{what}: {msg}")
+    return rc
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(I32P)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+@dataclass
+class QueryArrays:
+    vlab: np.ndarray
+    src: np.ndarray
+    dst: np.ndarray
+    elab: np.ndarray
+
+    @classmethod
+    def of(cls, q) -> "QueryArrays":
+        return cls(_i32(q.vlab), _i32(q.src), _i32(q.dst), _i32(q.elab))
+
+    @property
+    def k(self):
+        return int(self.vlab.shape[0])
+
+    @property
+    def qm(self):
+        return int(self.src.shape[0])
+
+    def desc(self) -> c_query_desc:
+        return c_query_desc(_p32(self.vlab), self.k, _p32(self.src), _p32(self.dst), _p32(self.elab), self.qm)
+
+
+class Result:
+    """Owner of a gsi_result handle."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gsi_result_destroy(self._h)
+            self._h = None
+
+    @property
+    def count(self) -> int:
+        c = ctypes.c_uint64()
+        _check(load().gsi_result_count(self._h, ctypes.byref(c)), "gsi_result_count")
+        return int(c.value)
+
+    @property
+    def k(self) -> int:
+        k = ctypes.c_int32()
+        _check(load().gsi_result_columns(self._h, ctypes.byref(k)), "gsi_result_columns")
+        return int(k.value)
+
+    def copy_to(self, ptr: int, max_rows: int) -> tuple[int, bool]:
+        """Copy into host or device memory at ptr; returns (rows, capped)."""
+        rows = ctypes.c_uint64()
+        rc = _check(load().gsi_result_copy(self._h, ptr, max_rows, ctypes.byref(rows)), "gsi_result_copy",
+                    ok=(GSI_OK, GSI_ECAPPED))
+        return int(rows.value), rc == GSI_ECAPPED
+
+    def rows(self, max_rows: int | None = None) -> np.ndarray:
+        """Materialised rows as a host int32 array [rows, k] (unordered)."""
+        n = self.count if max_rows is None else max_rows
+        out = np.empty((max(n, 1), self.k), np.int32)
+        got, _ = self.copy_to(out.ctypes.data, n)
+        return out[:got]
+
+
+class Graph:
+    """A labelled data graph resident on one GPU (gsi_graph_create)."""
+
+    def __init__(self, vlab, src, dst, elab, device: int = 0, stream=None):
+        L = load()
+        self._keep = [_i32(vlab), _i32(src), _i32(dst), _i32(elab)]
+        vl, s, d, e = self._keep
+        h = VP()
+        opts = c_graph_opts(device, _stream_handle(stream))
+        _check(L.gsi_graph_create(_p32(vl), vl.shape[0], _p32(s), _p32(d), _p32(e), s.shape[0],
+                                  ctypes.byref(opts), ctypes.byref(h)), "gsi_graph_create")
+        self._h = h.value
+        self._keep = None
+        self.device = device
+
+    @classmethod
+    def from_synth(cls, g, device: int = 0, stream=None) -> "Graph":
+        return cls(g.vlab, g.src, g.dst, g.elab, device, stream)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gsi_graph_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def info(self) -> c_graph_info:
+        i = c_graph_info()
+        _check(load().gsi_graph_get_info(self._h, ctypes.byref(i)), "gsi_graph_get_info")
+        return i
+
+    def export(self) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(off uint32[n*L+1], ci int32[2m], sig uint32[16, n]) copied to the host."""
+        i = self.info()
+        off = np.zeros(i.n * i.n_elabels + 1, np.uint32)
+        ci = np.zeros(max(2 * i.m, 1), np.int32)
+        sig = np.zeros((SIG_WORDS, i.n), np.uint32)
+        _check(load().gsi_graph_export(self._h, off.ctypes.data, ci.ctypes.data, sig.ctypes.data),
+               "gsi_graph_export")
+        return off, ci[: 2 * i.m], sig
+
+    def label_freq(self) -> np.ndarray:
+        L = self.info().n_elabels
+        out = np.zeros(L, np.uint64)
+        _check(load().gsi_graph_label_freq(self._h, out.ctypes.data_as(U64P), L), "gsi_graph_label_freq")
+        return out
+
+    def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
+              order=None, stats: c_stats | None = None) -> Result:
+        qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+        o = c_query_opts()
+        o.stream = _stream_handle(stream)
+        o.row_cap = row_cap
+        o.mem_budget = mem_budget
+        o.count_only = int(count_only)
+        o.semantics = 0
+        ordr = None
+        if order is not None:
+            ordr = _i32(order)
+            o.order = _p32(ordr)
+        if stats is not None:
+            o.stats = ctypes.pointer(stats)
+        h = VP()
+        _check(load().gsi_query_run(self._h, _p32(qa.vlab), qa.k, _p32(qa.src), _p32(qa.dst), _p32(qa.elab), qa.qm,
+                                    ctypes.byref(o), ctypes.byref(h)), "gsi_query_run")
+        return Result(h.value)
+
+    def filter(self, q, stream=None) -> tuple[np.ndarray, np.ndarray]:
+        """(bitmaps uint32[k, ceil(n/32)], counts uint64[k]) on the host."""
+        qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+        n = self.info().n
+        words = (n + 31) // 32
+        bm = np.zeros((qa.k, words), np.uint32)
+        cnt = np.zeros(qa.k, np.uint64)
+        _check(load().gsi_filter(self._h, _p32(qa.vlab), qa.k, _p32(qa.src), _p32(qa.dst), _p32(qa.elab), qa.qm,
+                                 bm.ctypes.data, cnt.ctypes.data, _stream_handle(stream)), "gsi_filter")
+        return bm, cnt
+
+    def join_step(self, M_ptr: int, R: int, t: int, cand_ptr: int, cols, labs, out_ptr: int, out_cap: int,
+                  stream=None) -> int:
+        """One join iteration on device buffers (pointers); returns the survivor count."""
+        c = _i32(cols)
+        l = _i32(labs)
+        cnt = ctypes.c_uint64()
+        _check(load().gsi_join_step(self._h, M_ptr, R, t, cand_ptr, _p32(c), _p32(l), c.shape[0], out_ptr, out_cap,
+                                    ctypes.byref(cnt), _stream_handle(stream)), "gsi_join_step")
+        return int(cnt.value)
+
+    def batch(self, queries, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
+              stats: c_stats | None = None) -> list:
+        qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
+        descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
+        outs = (VP * len(qas))()
+        sts = (ctypes.c_int32 * len(qas))()
+        o = c_batch_opts(_stream_handle(stream), row_cap, mem_budget, int(count_only),
+                         ctypes.pointer(stats) if stats is not None else None)
+        _check(load().gsi_batch_run(self._h, descs, len(qas), ctypes.byref(o), outs, sts), "gsi_batch_run")
+        res = []
+        for i in range(len(qas)):
+            res.append(Result(outs[i]) if sts[i] == GSI_OK else GsiError(sts[i], "batched query failed"))
+        return res
+
+
+def query_signatures(q) -> np.ndarray:
+    qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+    out = np.zeros((qa.k, SIG_WORDS), np.uint32)
+    _check(load().gsi_query_signatures(_p32(qa.vlab), qa.k, _p32(qa.src), _p32(qa.dst), _p32(qa.elab), qa.qm,
+                                       out.ctypes.data_as(U32P)), "gsi_query_signatures")
+    return out
+
+
+def plan_order(q, cand, freq) -> tuple[np.ndarray, np.ndarray]:
+    qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+    cand = np.ascontiguousarray(cand, np.uint64)
+    freq = np.ascontiguousarray(freq, np.uint64)
+    order = np.zeros(qa.k, np.int32)
+    first = np.zeros(qa.k, np.int32)
+    _check(load().gsi_plan_order(qa.k, _p32(qa.src), _p32(qa.dst), _p32(qa.elab), qa.qm, cand.ctypes.data_as(U64P),
+                                 freq.ctypes.data_as(U64P), freq.shape[0], _p32(order), _p32(first)),
+           "gsi_plan_order")
+    return order, first
+
+
+class Server:
+    """Continuous-batching server over a resident graph (gsi_server_*)."""
+
+    def __init__(self, graph: Graph, mem_budget: int = 0, n_streams: int = 4, row_cap: int = 0,
+                 count_only: bool = False):
+        self._graph = graph
+        h = VP()
+        o = c_server_opts(mem_budget, n_streams, row_cap, int(count_only))
+        _check(load().gsi_server_create(graph.handle, ctypes.byref(o), ctypes.byref(h)), "gsi_server_create")
+        self._h = h.value
+
+    def submit(self, q) -> int:
+        qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+        t = ctypes.c_uint64()
+        d = qa.desc()
+        _check(load().gsi_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)), "gsi_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(Result, latency_ms), or None if not finished within timeout_ms."""
+        h = VP()
+        lat = ctypes.c_double()
+        rc = load().gsi_server_poll(self._h, ticket, timeout_ms, ctypes.byref(h), ctypes.byref(lat))
+        if rc == GSI_EBUSY:
+            return None
+        _check(rc, "gsi_server_poll")
+        return Result(h.value), float(lat.value)
+
+    def cancel(self, ticket: int):
+        _check(load().gsi_server_cancel(self._h, ticket), "gsi_server_cancel")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gsi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def version() -> str:
+    return load().gsi_version().decode()
+
+
+def last_error() -> str:
+    return (load().gsi_last_error() or b"").decode()
