@@ -55,6 +55,25 @@ def parse_query_list(spec: str, n: int) -> list[int]:
     return [int(x) for x in spec.split(",") if x.strip()]
 
 
+def shard(items: list, rank: int, world: int) -> list:
+    """Round-robin share of independent queries for one rank (no data exchange)."""
+    return items[rank::world]
+
+
+def combine(local, world: int, device=None):
+    """All ranks' per-rank measurement vectors as a [world, len] numpy array."""
+    import torch
+    import torch.distributed as dist
+    t = torch.as_tensor(local, dtype=torch.float64)
+    if device is not None:
+        t = t.to(device)
+    if world <= 1:
+        return t.cpu().numpy()[None, :]
+    gathered = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(gathered, t)
+    return torch.stack(gathered).cpu().numpy()
+
+
 def cpu_sample(queries, n: int = 8, max_bound: float = 2e7) -> list[int]:
     """Deterministic CPU sample: the first n queries whose admission bound is <= max_bound."""
     idx = [i for i, q in enumerate(queries) if q.bound <= max_bound]
@@ -156,7 +175,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     queries = synth.queries(args.workload)
     if args.queries:
         queries = [queries[i] for i in parse_query_list(args.queries, len(queries))]
-    mine = queries[rank::world]
+    mine = shard(queries, rank, world)
     G = pkg.Graph.from_synth(g, device=local_rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -209,15 +228,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     filter_ms = sum(s.filter_ms for s in stats)
     filter_bytes = sum(s.filter_bytes for s in stats)
     kernels = sum(s.kernels for s in stats)
-    local = torch.tensor([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
-                          float(join_launches), filter_ms, float(filter_bytes), float(kernels)], dtype=torch.float64,
-                         device="cuda")
-    if world > 1:
-        gathered = [torch.zeros_like(local) for _ in range(world)]
-        dist.all_gather(gathered, local)
-        allv = torch.stack(gathered).cpu().numpy()
-    else:
-        allv = local.cpu().numpy()[None, :]
+    allv = combine([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
+                    float(join_launches), filter_ms, float(filter_bytes), float(kernels)], world, device="cuda")
     t_max_ms = float(allv[:, 0].max())
     tot_emb = float(allv[:, 1].sum())
     tot_q = float(allv[:, 2].sum())
