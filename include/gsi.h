@@ -191,6 +191,27 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
                          uint64_t *count, void *stream);
 
 /*
+ * gsi_join_step without any allocation, for callers that may not allocate
+ * device memory: a plugin running inside another runtime that owns all device
+ * memory and passes it only input and output buffers, a latency-critical path
+ * that must never wait on an allocator, or a process under a strict memory
+ * quota.  (The paper has no counterpart; it is a deployment variant of the
+ * join step above.)  Arguments, results and errors are those of
+ * gsi_join_step; the difference is where scratch lives: one file-scope device
+ * array of about 10.5 MB, held on every GPU that loads the library until the
+ * process exits.  Limits: R <= 2^20 rows and at most 2^28 candidate slots (sum
+ * over rows of |N(m_i[col0], lab0)| + 2); larger calls return GSI_EINVAL with
+ * a message.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and it keeps the previous call's contents (the
+ * survivor counter is cleared per call); calls that overlap on the GPU race
+ * on it and must be serialised by the caller.  Calls no allocator.
+ */
+gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, const uint32_t *cand,
+                                 const int32_t *col, const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
+                                 uint64_t *count, void *stream);
+
+/*
  * Alg. 2's matching order (host only, no GPU): cand[u] = |C(u)|, freq[l] for
  * l < n_labels.  order_out[k]: query vertex ids in join order; first_edge[k]:
  * for position p >= 1, the earlier query vertex whose edge to order[p] has the

@@ -25,7 +25,7 @@ SIG_WORDS = 16
 EXPORTED = [
     "gsi_graph_create", "gsi_graph_destroy", "gsi_graph_get_info", "gsi_graph_export", "gsi_graph_label_freq",
     "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_destroy",
-    "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_plan_order",
+    "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_join_step_noalloc", "gsi_plan_order",
     "gsi_batch_run", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
     "gsi_server_destroy", "gsi_last_error", "gsi_version",
 ]
@@ -137,6 +137,8 @@ def load(build_if_missing: bool = False):
     L.gsi_join_step.argtypes = [VP, VP, ctypes.c_uint64, ctypes.c_int32, VP, I32P, I32P, ctypes.c_int32, VP,
                                 ctypes.c_uint64, U64P, VP]
     L.gsi_join_step.restype = st
+    L.gsi_join_step_noalloc.argtypes = L.gsi_join_step.argtypes
+    L.gsi_join_step_noalloc.restype = st
     L.gsi_plan_order.argtypes = [ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, U64P, U64P, ctypes.c_int32,
                                  I32P, I32P]
     L.gsi_plan_order.restype = st
@@ -340,6 +342,18 @@ class Graph:
         cnt = ctypes.c_uint64()
         _check(load().gsi_join_step(self._h, M_ptr, R, t, cand_ptr, _p32(c), _p32(l), c.shape[0], out_ptr, out_cap,
                                     ctypes.byref(cnt), _stream_handle(stream)), "gsi_join_step")
+        return int(cnt.value)
+
+    def join_step_noalloc(self, M_ptr: int, R: int, t: int, cand_ptr: int, cols, labs, out_ptr: int, out_cap: int,
+                          stream=None) -> int:
+        """join_step with the library's static scratch array: no device allocation
+        (for callers that may not allocate); returns the survivor count."""
+        c = _i32(cols)
+        l = _i32(labs)
+        cnt = ctypes.c_uint64()
+        _check(load().gsi_join_step_noalloc(self._h, M_ptr, R, t, cand_ptr, _p32(c), _p32(l), c.shape[0], out_ptr,
+                                            out_cap, ctypes.byref(cnt), _stream_handle(stream)),
+               "gsi_join_step_noalloc")
         return int(cnt.value)
 
     def batch(self, queries, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
