@@ -67,16 +67,21 @@ typedef struct {
 typedef struct {
     int32_t n;           /* |V(G)| */
     int32_t n_elabels;   /* L: edge labels are 0..L-1 */
+    int32_t n_vlabels;   /* distinct vertex labels */
     int64_t m;           /* |E(G)| (undirected) */
     uint64_t device_bytes;   /* bytes held on the device by the graph */
     double build_ms;         /* device time of the build */
     /* device pointers, valid until gsi_graph_destroy (read-only):
        off  uint32[n*L + 1]: N(v,l) = ci[off[v*L+l] .. off[v*L+l+1])
-       ci   int32[2m]: neighbour lists, ascending within each (v,l)
+       ci   int32[2m]: neighbour lists; each N(v,l) sorted by (label rank of
+            the neighbour, neighbour id)
+       cl   uint16[2m]: label rank of ci[p] (index of its label among the
+            sorted distinct vertex labels)
        sig  uint32[16*n]: signature word w of vertex v at sig[w*n + v]
             (column-first, Sec. III-A); word 0 is the vertex label */
     const uint32_t *off;
     const int32_t *ci;
+    const uint16_t *cl;
     const uint32_t *sig;
 } gsi_graph_info;
 
@@ -89,7 +94,8 @@ typedef struct {
  *   vlab  int32[n]   vertex labels (any int32)
  *   src, dst, elab  int32[m]   edge i = {src[i], dst[i]} with label elab[i] >= 0
  * Errors: GSI_EINVAL for n < 1, m < 0, an id outside [0,n), a self-loop, a
- * negative edge label, 2m >= 2^32, or the same vertex pair given twice;
+ * negative edge label, 2m >= 2^32, more than 65535 distinct vertex labels, or
+ * the same vertex pair given twice;
  * GSI_ECUDA / GSI_ENOMEM for device failures.  *out is set only on GSI_OK.
  */
 gsi_status gsi_graph_create(const int32_t *vlab, int32_t n, const int32_t *src, const int32_t *dst,
@@ -98,9 +104,9 @@ void gsi_graph_destroy(gsi_graph *g);
 gsi_status gsi_graph_get_info(const gsi_graph *g, gsi_graph_info *info);
 /*
  * Copy the built layout out (host or device destinations; any may be NULL):
- * off uint32[n*L + 1], ci int32[2m], sig uint32[16*n] (column-first).
+ * off uint32[n*L + 1], ci int32[2m], cl uint16[2m], sig uint32[16*n].
  */
-gsi_status gsi_graph_export(const gsi_graph *g, uint32_t *off, int32_t *ci, uint32_t *sig);
+gsi_status gsi_graph_export(const gsi_graph *g, uint32_t *off, int32_t *ci, uint16_t *cl, uint32_t *sig);
 /* freq(l) for l in [0, L): number of undirected edges with label l. */
 gsi_status gsi_graph_label_freq(const gsi_graph *g, uint64_t *freq, int32_t max_labels);
 
@@ -178,17 +184,19 @@ gsi_status gsi_query_signatures(const int32_t *qvlab, int32_t k, const int32_t *
 
 /*
  * One join iteration (Alg. 3) on device buffers.  M: int32[R][t] row-major;
- * cand: C(u) bitmap (uint32[ceil(n/32)]); linking edges (col[j], lab[j]) for
- * j < d, with j = 0 the first edge e0 whose list bounds each row's output
- * (Alg. 4).  Writes rows (m || w) to out (int32[out_cap][t+1]) and the number
- * of rows found to *count (host).  Rows beyond out_cap are counted, not
- * written.  Scratch memory is allocated stream-ordered on `stream`.
- * Errors: GSI_EINVAL for t < 1, t >= 32, d < 1, d > t, a column outside
- * [0,t) or a label < 0.
+ * the new query vertex u has label ulabel and candidate set cand = C(u) as a
+ * bitmap (uint32[ceil(n/32)]); a candidate w must carry ulabel and have its
+ * bit set.  Linking edges (col[j], lab[j]) for j < d.  Each row's output is
+ * bounded by its shortest linking list restricted to ulabel (the Alg. 4
+ * bound, chosen per row).  Writes rows (m || w) to out (int32[out_cap][t+1])
+ * and the number of rows found to *count (host).  Rows beyond out_cap are
+ * counted, not written.  Scratch memory is allocated stream-ordered on
+ * `stream`.  Errors: GSI_EINVAL for t < 1, t >= 32, d < 1, d > t, a column
+ * outside [0,t) or a label < 0.
  */
 gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, const uint32_t *cand,
-                         const int32_t *col, const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
-                         uint64_t *count, void *stream);
+                         int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d, int32_t *out,
+                         uint64_t out_cap, uint64_t *count, void *stream);
 
 /*
  * gsi_join_step without any allocation, for callers that may not allocate
@@ -198,9 +206,9 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
  * quota.  (The paper has no counterpart; it is a deployment variant of the
  * join step above.)  Arguments, results and errors are those of
  * gsi_join_step; the difference is where scratch lives: one file-scope device
- * array of about 10.5 MB, held on every GPU that loads the library until the
+ * array of about 14.7 MB, held on every GPU that loads the library until the
  * process exits.  Limits: R <= 2^20 rows and at most 2^28 candidate slots (sum
- * over rows of |N(m_i[col0], lab0)| + 2); larger calls return GSI_EINVAL with
+ * over rows of the row's output bound + 2); larger calls return GSI_EINVAL with
  * a message.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the array and it keeps the previous call's contents (the
@@ -208,8 +216,8 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
  * on it and must be serialised by the caller.  Calls no allocator.
  */
 gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, const uint32_t *cand,
-                                 const int32_t *col, const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
-                                 uint64_t *count, void *stream);
+                                 int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d, int32_t *out,
+                                 uint64_t out_cap, uint64_t *count, void *stream);
 
 /*
  * Alg. 2's matching order (host only, no GPU): cand[u] = |C(u)|, freq[l] for

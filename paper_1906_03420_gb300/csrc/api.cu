@@ -54,6 +54,7 @@ gsi_status gsi_graph_create(const int32_t *vlab, int32_t n, const int32_t *src, 
     if (rc != GSI_OK) {
         if (g->off) cudaFree(g->off);
         if (g->ci) cudaFree(g->ci);
+        if (g->cl) cudaFree(g->cl);
         if (g->sig) cudaFree(g->sig);
         return rc;
     }
@@ -70,6 +71,7 @@ void gsi_graph_destroy(gsi_graph *g) {
     cudaDeviceSynchronize();
     cudaFree(g->off);
     cudaFree(g->ci);
+    cudaFree(g->cl);
     cudaFree(g->sig);
     if (cur >= 0) cudaSetDevice(cur);
     delete g;
@@ -87,11 +89,13 @@ gsi_status gsi_graph_get_info(const gsi_graph *g, gsi_graph_info *info) {
     info->build_ms = g->build_ms;
     info->off = g->off;
     info->ci = g->ci;
+    info->cl = g->cl;
     info->sig = g->sig;
+    info->n_vlabels = g->LV;
     return GSI_OK;
 }
 
-gsi_status gsi_graph_export(const gsi_graph *g, uint32_t *off, int32_t *ci, uint32_t *sig) {
+gsi_status gsi_graph_export(const gsi_graph *g, uint32_t *off, int32_t *ci, uint16_t *cl, uint32_t *sig) {
     if (!g) {
         set_error("gsi_graph_export: null graph");
         return GSI_EINVAL;
@@ -100,6 +104,7 @@ gsi_status gsi_graph_export(const gsi_graph *g, uint32_t *off, int32_t *ci, uint
     const uint64_t nseg = (uint64_t)g->n * (uint64_t)g->L;
     if (off) GSI_CUDA_TRY(cudaMemcpy(off, g->off, 4 * (nseg + 1), cudaMemcpyDefault));
     if (ci && g->m > 0) GSI_CUDA_TRY(cudaMemcpy(ci, g->ci, 8 * (uint64_t)g->m, cudaMemcpyDefault));
+    if (cl && g->m > 0) GSI_CUDA_TRY(cudaMemcpy(cl, g->cl, 4 * (uint64_t)g->m, cudaMemcpyDefault));
     if (sig) GSI_CUDA_TRY(cudaMemcpy(sig, g->sig, 4ull * GSI_SIG_WORDS * (uint64_t)g->n, cudaMemcpyDefault));
     return GSI_OK;
 }
@@ -239,8 +244,8 @@ gsi_status gsi_filter(gsi_graph *g, const int32_t *qvlab, int32_t k, const int32
 }
 
 gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, const uint32_t *cand,
-                         const int32_t *col, const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
-                         uint64_t *count, void *stream) {
+                         int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d, int32_t *out,
+                         uint64_t out_cap, uint64_t *count, void *stream) {
     GSI_API_BEGIN
     if (!g || !count || !col || !lab || (R > 0 && (!M || !cand)) || (out_cap > 0 && !out)) {
         set_error("gsi_join_step: null argument");
@@ -253,7 +258,8 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
     JoinStep s;
     s.t = t;
     s.d = d;
-    bool empty = false;
+    s.ulab = g->label_rank(ulabel);
+    bool empty = s.ulab < 0;
     for (int j = 0; j < d; ++j) {
         if (col[j] < 0 || col[j] >= t || lab[j] < 0) {
             set_error("gsi_join_step: column out of range or negative label");

@@ -46,7 +46,6 @@ __host__ __device__ inline uint32_t murmur3_pair(uint32_t a, uint32_t b, uint32_
     const uint32_t c1 = 0xcc9e2d51u, c2 = 0x1b873593u;
     uint32_t h = seed;
     uint32_t blk[2] = {a, b};
-#pragma unroll
     for (int i = 0; i < 2; ++i) {
         uint32_t k = blk[i];
         k *= c1;

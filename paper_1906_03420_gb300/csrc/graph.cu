@@ -7,7 +7,10 @@
 // With the label counts of the target workloads (8-16 edge labels) this costs
 // (L+1) * 4 bytes per vertex and replaces the paper's hashed PCSR groups,
 // which exist to save that space when labels number in the tens of thousands.
-// Each list is ascending, so membership is a binary search.
+// Each list N(v,l) is sorted by (label rank of the neighbour, neighbour id),
+// with the label ranks kept in a parallel uint16 array cl: the neighbours of
+// one vertex label form a contiguous, id-sorted sub-list, found by binary
+// search on cl, and membership inside it is a binary search on ci.
 //
 // Signatures (Sec. III-A): N = 512 bits = 16 words per vertex, stored
 // column-first (word w of vertex v at sig[w*n + v]) so a warp's 32 lanes read
@@ -15,6 +18,9 @@
 // bits).  Words 1..15 hold 240 two-bit groups: each (edge label, neighbour
 // label) pair of v is hashed to a group whose state goes 00 -> 01 -> 11 as the
 // first and second pair arrive.
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
 #include "scan.cuh"
 
@@ -59,25 +65,43 @@ __global__ void k_adjacent_equal(const uint64_t *__restrict__ keys, int64_t n, u
     if (__any_sync(FULL_MASK, dup) && (threadIdx.x & 31) == 0) atomicOr(flags, (unsigned)DUP_PAIR);
 }
 
-// Directed entry keys: ((v*L + l) << nb) | neighbour, two per edge.
-__global__ void k_csr_keys(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                           const int32_t *__restrict__ elab, int64_t m, int32_t L, int nb, uint64_t *__restrict__ keys) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t a = (uint32_t)src[e], b = (uint32_t)dst[e], l = (uint32_t)elab[e];
-        keys[2 * e] = ((a * (uint64_t)L + l) << nb) | b;
-        keys[2 * e + 1] = ((b * (uint64_t)L + l) << nb) | a;
+// Dense rank of each vertex label (binary search in the sorted distinct labels).
+__global__ void k_vertex_rank(const int32_t *__restrict__ vlab, int32_t n, const int32_t *__restrict__ uniq, int32_t LV,
+                              uint16_t *__restrict__ rank) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = vlab[v], lo = 0, hi = LV - 1;
+        while (lo < hi) {
+            int32_t mid = (lo + hi) >> 1;
+            if (uniq[mid] < x) lo = mid + 1;
+            else hi = mid;
+        }
+        rank[v] = (uint16_t)lo;
     }
 }
 
-// From sorted keys: ci[p] = neighbour, and off[s] = first position of segment s.
-__global__ void k_csr_fill(const uint64_t *__restrict__ keys, int64_t n2, int nb, uint64_t nseg,
-                           uint32_t *__restrict__ off, int32_t *__restrict__ ci) {
-    const uint64_t mask = (1ull << nb) - 1;
+// Directed entry keys: (((v*L + l) << lb | rank(neighbour)) << nb) | neighbour, two per edge.
+__global__ void k_csr_keys(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                           const int32_t *__restrict__ elab, const uint16_t *__restrict__ vrank, int64_t m, int32_t L,
+                           int lb, int nb, uint64_t *__restrict__ keys) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t a = (uint32_t)src[e], b = (uint32_t)dst[e], l = (uint32_t)elab[e];
+        keys[2 * e] = ((((a * (uint64_t)L + l) << lb) | vrank[b]) << nb) | b;
+        keys[2 * e + 1] = ((((b * (uint64_t)L + l) << lb) | vrank[a]) << nb) | a;
+    }
+}
+
+// From sorted keys: ci[p] = neighbour, cl[p] = its label rank, and off[s] =
+// first position of segment s = v*L + l.
+__global__ void k_csr_fill(const uint64_t *__restrict__ keys, int64_t n2, int lb, int nb, uint64_t nseg,
+                           uint32_t *__restrict__ off, int32_t *__restrict__ ci, uint16_t *__restrict__ cl) {
+    const uint64_t mask = (1ull << nb) - 1, lmask = (1ull << lb) - 1;
+    const int sh = lb + nb;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n2; p += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = keys[p];
         ci[p] = (int32_t)(k & mask);
-        uint64_t s = k >> nb;
-        uint64_t prev = p == 0 ? 0 : (keys[p - 1] >> nb) + 1;
+        cl[p] = (uint16_t)((k >> nb) & lmask);
+        uint64_t s = k >> sh;
+        uint64_t prev = p == 0 ? 0 : (keys[p - 1] >> sh) + 1;
         for (uint64_t x = prev; x <= s; ++x) off[x] = (uint32_t)p;
         if (p == n2 - 1)
             for (uint64_t x = s + 1; x <= nseg; ++x) off[x] = (uint32_t)n2;
@@ -191,12 +215,35 @@ gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32
         return GSI_EINVAL;
     }
     const int32_t L = maxlab < 0 ? 1 : maxlab + 1;
+    // sorted distinct vertex labels (host): dense ranks for the sub-list order
+    std::vector<int32_t> uniq;
+    {
+        int32_t mn = vlab[0], mx = vlab[0];
+        for (int32_t v = 1; v < n; ++v) { mn = std::min(mn, vlab[v]); mx = std::max(mx, vlab[v]); }
+        if ((int64_t)mx - (int64_t)mn < (1 << 24)) {
+            std::vector<uint8_t> seen((size_t)((int64_t)mx - mn + 1), 0);
+            for (int32_t v = 0; v < n; ++v) seen[(size_t)((int64_t)vlab[v] - mn)] = 1;
+            for (size_t i = 0; i < seen.size(); ++i)
+                if (seen[i]) uniq.push_back((int32_t)((int64_t)mn + (int64_t)i));
+        } else {
+            uniq.assign(vlab, vlab + n);
+            std::sort(uniq.begin(), uniq.end());
+            uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        }
+    }
+    if (uniq.size() > 65535) {
+        cleanup_inputs();
+        set_error("gsi_graph_create: more than 65535 distinct vertex labels");
+        return GSI_EINVAL;
+    }
+    const int32_t LV = (int32_t)uniq.size();
     const int nb = ceil_log2_bits((uint64_t)(n > 1 ? n - 1 : 1));
+    const int lb = ceil_log2_bits((uint64_t)(LV > 1 ? LV - 1 : 1));
     const uint64_t nseg = (uint64_t)n * (uint64_t)L;
     const int sb = ceil_log2_bits(nseg - 1);
-    if (sb + nb > 64 || nseg + 1 >= ((uint64_t)1 << 34)) {
+    if (sb + lb + nb > 64 || nseg + 1 >= ((uint64_t)1 << 34)) {
         cleanup_inputs();
-        set_error("gsi_graph_create: n * L too large for the label-partitioned layout");
+        set_error("gsi_graph_create: n * L * labels too large for the label-partitioned layout");
         return GSI_EINVAL;
     }
 
@@ -219,14 +266,24 @@ gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32
     }
 
     // CSR
-    g->n = n; g->m = m; g->L = L; g->nwords = (n + 31) / 32;
+    g->n = n; g->m = m; g->L = L; g->LV = LV; g->nwords = (n + 31) / 32;
+    g->vlabels = uniq;
     GSI_CUDA_TRY(cudaMallocAsync(&g->off, sizeof(uint32_t) * (size_t)(nseg + 1), st));
     GSI_CUDA_TRY(cudaMallocAsync(&g->ci, sizeof(int32_t) * (size_t)(2 * m + 1), st));
+    GSI_CUDA_TRY(cudaMallocAsync(&g->cl, sizeof(uint16_t) * (size_t)(2 * m + 1), st));
     GSI_CUDA_TRY(cudaMallocAsync(&g->sig, sizeof(uint32_t) * (size_t)GSI_SIG_WORDS * (size_t)n, st));
     if (m > 0) {
-        k_csr_keys<<<grid_for(m), NT, 0, st>>>(d_src, d_dst, d_elab, m, L, nb, keys);
-        GSI_TRY(radix_sort_u64(keys, tmp, 2 * m, sb + nb, st));
-        k_csr_fill<<<grid_for(2 * m), NT, 0, st>>>(keys, 2 * m, nb, nseg, g->off, g->ci);
+        int32_t *d_uniq = nullptr;
+        uint16_t *d_vrank = nullptr;
+        GSI_CUDA_TRY(cudaMallocAsync(&d_uniq, sizeof(int32_t) * (size_t)LV, st));
+        GSI_CUDA_TRY(cudaMallocAsync(&d_vrank, sizeof(uint16_t) * (size_t)n, st));
+        GSI_CUDA_TRY(cudaMemcpyAsync(d_uniq, uniq.data(), sizeof(int32_t) * (size_t)LV, cudaMemcpyHostToDevice, st));
+        k_vertex_rank<<<grid_for(n), NT, 0, st>>>(d_vlab, n, d_uniq, LV, d_vrank);
+        k_csr_keys<<<grid_for(m), NT, 0, st>>>(d_src, d_dst, d_elab, d_vrank, m, L, lb, nb, keys);
+        GSI_TRY(radix_sort_u64(keys, tmp, 2 * m, sb + lb + nb, st));
+        k_csr_fill<<<grid_for(2 * m), NT, 0, st>>>(keys, 2 * m, lb, nb, nseg, g->off, g->ci, g->cl);
+        cudaFreeAsync(d_uniq, st);
+        cudaFreeAsync(d_vrank, st);
     } else {
         k_fill_u32<<<grid_for((int64_t)nseg + 1), NT, 0, st>>>(g->off, nseg + 1, 0u);
     }
@@ -259,7 +316,7 @@ gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32
     cudaEventDestroy(e1);
     g->build_ms = ms;
     g->device_bytes = sizeof(uint32_t) * (nseg + 1) + sizeof(int32_t) * (uint64_t)(2 * m + 1) +
-                      sizeof(uint32_t) * GSI_SIG_WORDS * (uint64_t)n;
+                      sizeof(uint16_t) * (uint64_t)(2 * m + 1) + sizeof(uint32_t) * GSI_SIG_WORDS * (uint64_t)n;
     return GSI_OK;
 }
 

@@ -14,11 +14,15 @@ struct gsi_graph {
     int32_t n = 0;
     int64_t m = 0;
     int32_t L = 1;              // edge labels 0..L-1
+    int32_t LV = 1;             // distinct vertex labels
     int32_t nwords = 0;         // ceil(n / 32): words of one candidate bitmap
     uint32_t *off = nullptr;    // [n*L + 1]
-    int32_t *ci = nullptr;      // [2m]
+    int32_t *ci = nullptr;      // [2m], each N(v,l) sorted by (label rank of neighbour, id)
+    uint16_t *cl = nullptr;     // [2m], label rank of ci[p]
     uint32_t *sig = nullptr;    // [16 * n], column-first
     std::vector<uint64_t> freq; // [L]
+    std::vector<int32_t> vlabels;   // sorted distinct vertex labels; rank = index
+    int32_t label_rank(int32_t label) const;   // -1 if no vertex carries it
     uint64_t device_bytes = 0;
     double build_ms = 0;
 };
@@ -53,7 +57,8 @@ int64_t seed_scratch_words(const gsi_graph *g);
 // ------------------------------------------------------------------ join
 struct JoinStep {
     int32_t t = 0;                       // columns of M
-    int32_t d = 0;                       // linking edges; [0] is e0
+    int32_t ulab = 0;                    // label rank of the new query vertex
+    int32_t d = 0;                       // linking edges; [0] is e0 (Alg. 4)
     int32_t col[GSI_MAX_QUERY_VERTICES];
     int32_t lab[GSI_MAX_QUERY_VERTICES];
     int32_t perm[GSI_MAX_QUERY_VERTICES + 1];   // output position of each column
@@ -64,7 +69,8 @@ constexpr int JOIN_VT = 4;
 constexpr int JOIN_NV = JOIN_NT * JOIN_VT;
 constexpr int JOIN_ROW_WEIGHT = 2;      // slots charged per row (row staging work)
 
-// Exclusive scan over rows of (|N(M[i][col0], lab0)| + W): F[0..R], F[R] = total slots.
+// Exclusive scan over rows of (cap_i + W): F[0..R], F[R] = total slots, where
+// cap_i is the shortest label sub-list of row i's linking lists.
 gsi_status launch_join_scan(const gsi_graph *g, const int32_t *M, uint64_t R, const JoinStep &s, uint64_t *F,
                             uint64_t *scratch, cudaStream_t st);
 int64_t join_scan_scratch(uint64_t R);

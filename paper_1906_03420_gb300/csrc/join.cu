@@ -1,28 +1,37 @@
 // One join iteration (Sec. V, Algs. 3-4) as three launches:
 //
-//   1. scan   F[i] = sum_{r<i} (|N(m_r[u0'], l0)| + W): Alg. 4's exclusive
-//             prefix sum of each row's output bound, plus W "row slots" per
-//             row that pay for staging the row (load balancing, below).
+//   1. scan   F[i] = sum_{r<i} (cap_r + W), where cap_r bounds row r's output
+//             (Alg. 4's preallocation bound), plus W "row slots" per row that
+//             pay for staging the row (load balancing, below).
 //   2. part   for every tile of NV consecutive slots, its first row.
 //   3. join   the fused kernel: one CTA per tile of NV slots.
 //
+// Output bound.  Every neighbour list N(v,l) is stored sorted by (label rank
+// of the neighbour, neighbour id), so the neighbours of v via l that carry
+// the new query vertex's label form one contiguous, id-sorted sub-list.  Any
+// survivor w of row i lies in that sub-list of every linking edge, so each
+// row takes as its candidate list (and output bound, Alg. 4) the shortest of
+// these sub-lists; Alg. 4's global choice of the least frequent edge label is
+// the same bound taken once for all rows.
+//
 // Work decomposition.  Instead of the paper's warp-per-row with a 4-layer
 // balance scheme and dynamically launched child kernels (Sec. VI-A), every
-// candidate w of N(m_i[u0'], l0) is one slot of a flat index space whose row
-// offsets are F, and each CTA takes a fixed NV slots.  A hub row with 10^5
+// candidate of every row is one slot of a flat index space whose row offsets
+// are F, and each CTA takes a fixed NV slots.  A hub row with 10^5
 // candidates is spread over many CTAs; rows with one candidate are packed
 // NV/W to a CTA.  The W per-row slots bound the rows one CTA stages, so its
 // shared memory holds every row it touches.
 //
 // Per CTA (Sec. V "GPU-friendly set operation"):
 //   * the partial matches m_i of its rows are staged in shared memory with
-//     the located bounds of every neighbour list they need (small lists);
-//   * slots read consecutive elements of N(v, l0) (coalesced medium list);
+//     the bounds of every label sub-list they need (small lists);
+//   * a slot -> row map is built with one block-wide max-scan;
+//   * slots read consecutive elements of the row's candidate sub-list
+//     (coalesced medium list);
 //   * C(u) is probed as a bitset, one 4-byte load per candidate (large list);
 //   * set subtraction (w not in m_i) is checked against the staged row;
-//   * the other linking edges test w in N(m_i[u_j'], l_j) by binary search
-//     in the ascending list (the intersection), only for candidates that
-//     survived the cheaper checks;
+//   * the other linking edges test w in their sub-list by binary search (the
+//     intersection), only for candidates that survived the cheaper checks;
 //   * survivors are compacted with one block-wide prefix sum and one global
 //     atomic per CTA, then written once as rows of M' (Prealloc-Combine: the
 //     join runs once; the output buffer is sized by F's total).
@@ -32,17 +41,78 @@
 namespace gsi {
 namespace {
 
-struct CapProducer {
+// [lo, hi) of the entries with label rank `r` inside the (rank, id)-sorted list cl[a..b)
+__device__ inline void label_range(const uint16_t *__restrict__ cl, uint32_t a, uint32_t b, uint32_t r,
+                                   uint32_t *lo, uint32_t *hi) {
+    uint32_t l = a, h = b;
+    while (l < h) {
+        uint32_t m = (l + h) >> 1;
+        if (__ldg(cl + m) < r) l = m + 1;
+        else h = m;
+    }
+    const uint32_t s = l;
+    h = b;
+    while (l < h) {
+        uint32_t m = (l + h) >> 1;
+        if (__ldg(cl + m) <= r) l = m + 1;
+        else h = m;
+    }
+    *lo = s;
+    *hi = l;
+}
+
+struct StepDev {
+    int32_t t, d, L, ulab;
+    int32_t col[GSI_MAX_QUERY_VERTICES];
+    int32_t lab[GSI_MAX_QUERY_VERTICES];
+};
+
+// Row i's output bound: the shortest label sub-list over its linking edges.
+__device__ inline uint32_t row_bound(const StepDev &s, const int32_t *__restrict__ row, const uint32_t *__restrict__ off,
+                                     const uint16_t *__restrict__ cl) {
+    uint32_t best = 0xffffffffu;
+    for (int j = 0; j < s.d; ++j) {
+        uint64_t seg = (uint64_t)(uint32_t)row[s.col[j]] * (uint64_t)s.L + (uint64_t)s.lab[j];
+        uint32_t a = __ldg(off + seg), b = __ldg(off + seg + 1), lo, hi;
+        label_range(cl, a, b, (uint32_t)s.ulab, &lo, &hi);
+        best = min(best, hi - lo);
+        if (best == 0) break;
+    }
+    return best;
+}
+
+// Reduce pass: stores each row's bound for the down pass.
+struct CapStoreProducer {
     const int32_t *M;
-    int32_t t, c0, l0, L;
     const uint32_t *off;
+    const uint16_t *cl;
+    uint32_t *caps;
     uint64_t W;
+    StepDev s;
     __device__ uint64_t operator()(int64_t i) const {
-        int32_t v = M[i * t + c0];
-        uint64_t s = (uint64_t)(uint32_t)v * (uint64_t)L + (uint64_t)l0;
-        return (uint64_t)(__ldg(off + s + 1) - __ldg(off + s)) + W;
+        uint32_t c = row_bound(s, M + i * s.t, off, cl);
+        caps[i] = c;
+        return (uint64_t)c + W;
     }
 };
+struct CapLoadProducer {
+    const uint32_t *caps;
+    uint64_t W;
+    __device__ uint64_t operator()(int64_t i) const { return (uint64_t)caps[i] + W; }
+};
+
+template <typename P1, typename P2, typename Wr>
+cudaError_t two_producer_scan(P1 p1, P2 p2, int64_t n, Wr write, uint64_t *scratch, cudaStream_t st) {
+    if (n <= 0) {
+        k_scan_empty<uint64_t, Wr><<<1, 1, 0, st>>>(write);
+        return cudaGetLastError();
+    }
+    int64_t nb = scan_blocks(n);
+    k_scan_reduce<uint64_t, P1><<<(unsigned)nb, SCAN_NT, 0, st>>>(p1, n, scratch);
+    k_scan_spine<uint64_t><<<1, 1024, 0, st>>>(scratch, nb);
+    k_scan_down<uint64_t, P2, Wr><<<(unsigned)nb, SCAN_NT, 0, st>>>(p2, n, scratch, nb, write);
+    return cudaGetLastError();
+}
 
 __global__ void k_partition(const uint64_t *__restrict__ F, int64_t R, uint64_t total, int64_t ntiles,
                             int64_t *__restrict__ part) {
@@ -67,25 +137,55 @@ struct JoinArgs {
     const int64_t *part;
     const uint32_t *off;
     const int32_t *ci;
+    const uint16_t *cl;
     const uint32_t *cand;
     int32_t *out;
     uint64_t out_cap;
     unsigned long long *out_count;
     unsigned long long *stats;
-    int32_t t, d, L, W, rmax, count_only;
-    int32_t col[GSI_MAX_QUERY_VERTICES];
-    int32_t lab[GSI_MAX_QUERY_VERTICES];
-    int32_t perm[GSI_MAX_QUERY_VERTICES + 1];
+    int32_t W, rmax, count_only;
+    StepDev s;
+    int32_t iperm[GSI_MAX_QUERY_VERTICES + 1];   // output column oc holds input position iperm[oc]
 };
+
+template <int NT>
+__device__ inline int block_inclusive_max(int v, int *wt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, v, o);
+        if (lane >= o) v = max(v, y);
+    }
+    if (lane == 31) wt[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NW ? wt[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL_MASK, w, o);
+            if (lane >= o) w = max(w, y);
+        }
+        if (lane < NW) wt[lane] = w;
+    }
+    __syncthreads();
+    int r = warp > 0 ? max(v, wt[warp - 1]) : v;
+    __syncthreads();
+    return r;
+}
 
 template <int NT, int VT>
 __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a) {
     constexpr int NV = NT * VT;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long wt[NT / 32];
+    __shared__ int wti[NT / 32];
     __shared__ unsigned long long gbase_s;
+    __shared__ uint16_t rowmap[NV];
+    __shared__ int2 wsurv[NT / 32][32 * VT];          // per-warp survivors (local row, w)
+    __shared__ unsigned wcnt[NT / 32 + 1];
 
-    const int t = a.t, dm1 = a.d - 1;
+    const int t = a.s.t, d = a.s.d, dm1 = d - 1;
     uint64_t *Fs = reinterpret_cast<uint64_t *>(smem);                 // rmax + 1
     uint32_t *base0 = reinterpret_cast<uint32_t *>(Fs + a.rmax + 1);    // rmax
     uint32_t *lst = base0 + a.rmax;                                     // rmax * 2 * dm1
@@ -97,24 +197,63 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
     const int64_t r_hi = min(a.part[blockIdx.x + 1], a.R - 1);
     const int nr = (int)(r_hi - r_lo + 1);
 
-    // ---- stage the tile's rows: values, first-edge list start, other lists
-    unsigned long long bytes = 0;
+    // ---- stage the tile's rows: values, candidate sub-list, other sub-lists
+    for (int x = threadIdx.x; x < NV; x += NT) rowmap[x] = 0;
     for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = a.F[r_lo + lr];
+    __syncthreads();
+    unsigned long long bytes = 0;
     for (int lr = threadIdx.x; lr < nr; lr += NT) {
         const int32_t *row = a.M + (r_lo + lr) * (int64_t)t;
         int32_t *rv = rowv + lr * t;
         for (int c = 0; c < t; ++c) rv[c] = row[c];
-        uint64_t seg0 = (uint64_t)(uint32_t)rv[a.col[0]] * (uint64_t)a.L + (uint64_t)a.lab[0];
-        base0[lr] = __ldg(a.off + seg0);
+        // the row's lists: the shortest label sub-list supplies candidates
+        uint32_t lo[GSI_MAX_QUERY_VERTICES], len[GSI_MAX_QUERY_VERTICES];
+        uint32_t best = 0xffffffffu;
+        int jb = 0;
         uint64_t lsum = 0;
-        for (int j = 1; j <= dm1; ++j) {
-            uint64_t seg = (uint64_t)(uint32_t)rv[a.col[j]] * (uint64_t)a.L + (uint64_t)a.lab[j];
-            uint32_t lo = __ldg(a.off + seg), hi = __ldg(a.off + seg + 1);
-            lst[(lr * dm1 + (j - 1)) * 2] = lo;
-            lst[(lr * dm1 + (j - 1)) * 2 + 1] = hi - lo;
-            lsum += hi - lo;
+        for (int j = 0; j < d; ++j) {
+            uint64_t seg = (uint64_t)(uint32_t)rv[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+            uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1), h;
+            label_range(a.cl, x0, x1, (uint32_t)a.s.ulab, &lo[j], &h);
+            len[j] = h - lo[j];
+            if (len[j] < best) { best = len[j]; jb = j; }
+            lsum += len[j];
+            if (best == 0) break;
         }
-        if (a.stats && Fs[lr] >= s0) bytes += 4ull * t + 8ull * a.d + 4ull * lsum;   // row owned by this tile
+        base0[lr] = lo[jb];
+        int q = 0;
+        for (int j = 0; j < d && best > 0; ++j) {
+            if (j == jb) continue;
+            lst[(lr * dm1 + q) * 2] = lo[j];
+            lst[(lr * dm1 + q) * 2 + 1] = len[j];
+            ++q;
+        }
+        const uint64_t fr = Fs[lr];
+        if (fr > s0 && fr < s1) rowmap[fr - s0] = (uint16_t)lr;       // first slot of the row in this tile
+        if (a.stats && fr >= s0) bytes += 4ull * t + 8ull * d + 4ull * (lsum - best);   // row owned by this tile
+    }
+    __syncthreads();
+    {   // slot -> row: inclusive max-scan of the row-start marks
+        int v[VT];
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < VT; ++k) {
+            v[k] = rowmap[threadIdx.x * VT + k];
+            m = max(m, v[k]);
+            v[k] = m;
+        }
+        const int incl = block_inclusive_max<NT>(m, wti);   // max over threads 0..tid
+        const int before = __shfl_up_sync(FULL_MASK, incl, 1);
+        // exclusive prefix for this thread = inclusive max of the previous thread
+        int ex = 0;
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane > 0) ex = before;
+            else if (warp > 0) ex = wti[warp - 1];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < VT; ++k) rowmap[threadIdx.x * VT + k] = (uint16_t)max(ex, v[k]);
     }
     __syncthreads();
 
@@ -129,50 +268,70 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
         wv[k] = 0;
         lrv[k] = 0;
         if (s >= s1) continue;
-        int lo = 0, hi = nr - 1;        // row of slot s: largest lr with Fs[lr] <= s
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (Fs[mid] <= s) lo = mid;
-            else hi = mid - 1;
-        }
-        const int64_t p = (int64_t)(s - Fs[lo]) - a.W;
+        const int lr = rowmap[s - s0];
+        const int64_t p = (int64_t)(s - Fs[lr]) - a.W;
         if (p < 0) continue;            // a row-staging slot
         ++items;
-        const int32_t w = __ldg(a.ci + (uint64_t)base0[lo] + (uint64_t)p);
+        const int32_t w = __ldg(a.ci + (uint64_t)base0[lr] + (uint64_t)p);
         bool ok = (__ldg(a.cand + (w >> 5)) >> (w & 31)) & 1u;
-        const int32_t *rv = rowv + lo * t;
+        const int32_t *rv = rowv + lr * t;
         for (int c = 0; c < t && ok; ++c) ok = rv[c] != w;
         for (int j = 0; j < dm1 && ok; ++j) {
-            const uint32_t *ls = lst + (lo * dm1 + j) * 2;
+            const uint32_t *ls = lst + (lr * dm1 + j) * 2;
             ok = sorted_contains(a.ci + ls[0], ls[1], w);
         }
         wv[k] = w;
-        lrv[k] = lo;
+        lrv[k] = lr;
         if (ok) okmask |= 1u << k;
     }
 
-    // ---- compaction: block prefix sum + one atomic per CTA, then write once
-    unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(__popc(okmask), wt, &tot);
-    if (threadIdx.x == 0) gbase_s = tot ? atomicAdd(a.out_count, tot) : 0ull;
-    __syncthreads();
-    if (!a.count_only) {
-        uint64_t idx = gbase_s + ex;
+    // ---- compaction: warp ballots, one atomic per CTA, then each warp writes
+    // its survivors' rows as one contiguous, coalesced run of M'
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned nw = 0;
+    const unsigned lt = lanemask_lt();
 #pragma unroll
-        for (int k = 0; k < VT; ++k) {
-            if (!((okmask >> k) & 1u)) continue;
-            if (idx < a.out_cap) {
-                int32_t *dst = a.out + idx * (uint64_t)(t + 1);
-                const int32_t *rv = rowv + lrv[k] * t;
-                for (int c = 0; c < t; ++c) dst[a.perm[c]] = rv[c];
-                dst[a.perm[t]] = wv[k];
-            }
-            ++idx;
+    for (int k = 0; k < VT; ++k) {
+        const bool ok = (okmask >> k) & 1u;
+        const unsigned b = __ballot_sync(FULL_MASK, ok);
+        if (ok) wsurv[warp][nw + __popc(b & lt)] = make_int2(lrv[k], wv[k]);
+        nw += __popc(b);
+    }
+    if (lane == 0) wcnt[warp] = nw;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            unsigned c = wcnt[w];
+            wcnt[w] = run;
+            run += c;
+        }
+        wcnt[NT / 32] = run;
+        gbase_s = run ? atomicAdd(a.out_count, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    const unsigned nsurv = wcnt[NT / 32];
+    if (!a.count_only && nw > 0) {
+        const uint64_t base = gbase_s + wcnt[warp];
+        const uint64_t room = a.out_cap > base ? a.out_cap - base : 0;
+        const unsigned nrow = (unsigned)min((uint64_t)nw, room);
+        const int W1 = t + 1;
+        const unsigned nel = nrow * (unsigned)W1;
+        int32_t *dst = a.out + base * (uint64_t)W1;
+        int row = lane / W1, colx = lane % W1;
+        const int qrow = 32 / W1, qcol = 32 % W1;
+        for (unsigned e = lane; e < nel; e += 32) {
+            const int2 sv = wsurv[warp][row];
+            const int c = a.iperm[colx];
+            dst[e] = c == t ? sv.y : rowv[sv.x * t + c];
+            row += qrow;
+            colx += qcol;
+            if (colx >= W1) { colx -= W1; ++row; }
         }
     }
     if (a.stats) {
         bytes += 8ull * items;                                    // list element + bitmap probe
-        if (!a.count_only) bytes += 4ull * (t + 1) * __popc(okmask);
+        if (!a.count_only && threadIdx.x == 0) bytes += 4ull * (t + 1) * nsurv;
         unsigned long long bsum = block_sum<NT, unsigned long long>(bytes, wt);
         unsigned long long isum = block_sum<NT, unsigned long long>(items, wt);
         if (threadIdx.x == 0) {
@@ -184,14 +343,30 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
 
 int g_smem_set[64];
 
+StepDev step_dev(const gsi_graph *g, const JoinStep &s) {
+    StepDev d;
+    d.t = s.t;
+    d.d = s.d;
+    d.L = g->L;
+    d.ulab = s.ulab;
+    for (int i = 0; i < GSI_MAX_QUERY_VERTICES; ++i) {
+        d.col[i] = i < s.d ? s.col[i] : 0;
+        d.lab[i] = i < s.d ? s.lab[i] : 0;
+    }
+    return d;
+}
+
 }  // namespace
 
-int64_t join_scan_scratch(uint64_t R) { return scan_blocks((int64_t)R) + 1; }
+int64_t join_scan_scratch(uint64_t R) { return scan_blocks((int64_t)R) + 1 + ((int64_t)R + 1) / 2 + 1; }
 
 gsi_status launch_join_scan(const gsi_graph *g, const int32_t *M, uint64_t R, const JoinStep &s, uint64_t *F,
                             uint64_t *scratch, cudaStream_t st) {
-    CapProducer p{M, s.t, s.col[0], s.lab[0], g->L, g->off, (uint64_t)JOIN_ROW_WEIGHT};
-    GSI_CUDA_TRY(device_scan<uint64_t>(p, (int64_t)R, StoreWriter<uint64_t>{F}, scratch, st));
+    // scratch: [scan block sums][per-row bounds as uint32]
+    uint32_t *caps = reinterpret_cast<uint32_t *>(scratch + scan_blocks((int64_t)R) + 1);
+    CapStoreProducer p1{M, g->off, g->cl, caps, (uint64_t)JOIN_ROW_WEIGHT, step_dev(g, s)};
+    CapLoadProducer p2{caps, (uint64_t)JOIN_ROW_WEIGHT};
+    GSI_CUDA_TRY(two_producer_scan(p1, p2, (int64_t)R, StoreWriter<uint64_t>{F}, scratch, st));
     return GSI_OK;
 }
 
@@ -222,16 +397,14 @@ gsi_status launch_join(const gsi_graph *g, const int32_t *M, uint64_t R, const J
     }
     JoinArgs a;
     a.M = M; a.R = (int64_t)R; a.F = F; a.total = total; a.part = part;
-    a.off = g->off; a.ci = g->ci; a.cand = cand;
+    a.off = g->off; a.ci = g->ci; a.cl = g->cl; a.cand = cand;
     a.out = out; a.out_cap = out_cap; a.out_count = out_count; a.stats = stats;
-    a.t = s.t; a.d = s.d; a.L = g->L; a.W = JOIN_ROW_WEIGHT;
+    a.W = JOIN_ROW_WEIGHT;
     a.rmax = JOIN_NV / JOIN_ROW_WEIGHT + 2;
     a.count_only = count_only;
-    for (int i = 0; i < GSI_MAX_QUERY_VERTICES; ++i) {
-        a.col[i] = i < s.d ? s.col[i] : 0;
-        a.lab[i] = i < s.d ? s.lab[i] : 0;
-    }
-    for (int i = 0; i <= GSI_MAX_QUERY_VERTICES; ++i) a.perm[i] = i <= s.t ? s.perm[i] : i;
+    a.s = step_dev(g, s);
+    for (int i = 0; i <= GSI_MAX_QUERY_VERTICES; ++i) a.iperm[i] = i;
+    for (int c = 0; c <= s.t; ++c) a.iperm[s.perm[c]] = c;
     size_t sm = join_smem(a.rmax, s.t, s.d);
     int dev = 0;
     cudaGetDevice(&dev);

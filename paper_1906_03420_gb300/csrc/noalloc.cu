@@ -8,14 +8,14 @@
 // stream-ordered pool can still have to grow); a process under a strict
 // device-memory quota where an allocation in the middle of a request could
 // fail.  For them this entry point runs the same kernels as gsi_join_step, but
-// every scratch buffer (the row-bound scan, its block sums, the tile partition
-// and the survivor counter) lives in one file-scope __device__ array of fixed
+// every scratch buffer (the row-bound scan, its block sums and per-row bounds,
+// the tile partition and the survivor counter) lives in one file-scope __device__ array of fixed
 // size.  The caller still provides the input table, the candidate bitmap and
 // the output buffer.
 //
 // Limits: at most 2^20 input rows and 2^28 candidate slots (the sum over rows
-// of the first-edge list length plus two per row) per call.  The array takes
-// about 10.5 MB on every GPU that loads the library, until the process exits.
+// of the row's output bound plus two) per call.  The array takes
+// about 14.7 MB on every GPU that loads the library, until the process exits.
 // Every call shares it and it keeps the previous call's contents; the
 // survivor counter is cleared on each call.  Calls that overlap on the GPU
 // (concurrent streams or host threads) race on the array and must be
@@ -34,7 +34,8 @@ constexpr uint64_t NA_MAX_SLOTS = 1ull << 28;
 // layout in 8-byte words
 constexpr uint64_t NA_F = 0;                                              // F: rows + 1
 constexpr uint64_t NA_SCAN = NA_F + NA_MAX_ROWS + 1;                      // scan block sums
-constexpr uint64_t NA_SCAN_WORDS = (NA_MAX_ROWS + SCAN_NV - 1) / SCAN_NV + 1;
+// block sums (one per scan block, plus the total) and each row's bound as uint32
+constexpr uint64_t NA_SCAN_WORDS = (NA_MAX_ROWS + SCAN_NV - 1) / SCAN_NV + 1 + (NA_MAX_ROWS + 1) / 2 + 1;
 constexpr uint64_t NA_PART = NA_SCAN + NA_SCAN_WORDS;                     // tile partition
 constexpr uint64_t NA_PART_WORDS = NA_MAX_SLOTS / JOIN_NV + 2;
 constexpr uint64_t NA_COUNT = NA_PART + NA_PART_WORDS;                    // survivor counter
@@ -72,8 +73,9 @@ gsi_status scratch_address(int dev, unsigned long long **out) {
 using namespace gsi;
 
 extern "C" gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t,
-                                            const uint32_t *cand, const int32_t *col, const int32_t *lab, int32_t d,
-                                            int32_t *out, uint64_t out_cap, uint64_t *count, void *stream) {
+                                            const uint32_t *cand, int32_t ulabel, const int32_t *col,
+                                            const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
+                                            uint64_t *count, void *stream) {
     if (!g || !count || !col || !lab || (R > 0 && (!M || !cand)) || (out_cap > 0 && !out)) {
         set_error("gsi_join_step_noalloc: null argument");
         return GSI_EINVAL;
@@ -86,10 +88,15 @@ extern "C" gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint
         set_error("gsi_join_step_noalloc: more than 2^20 input rows (the static scratch limit)");
         return GSI_EINVAL;
     }
+    if (join_scan_scratch(R) > (int64_t)NA_SCAN_WORDS) {
+        set_error("gsi_join_step_noalloc: scan scratch larger than the static array");
+        return GSI_EINVAL;
+    }
     JoinStep s;
     s.t = t;
     s.d = d;
-    bool empty = false;
+    s.ulab = g->label_rank(ulabel);
+    bool empty = s.ulab < 0;
     for (int j = 0; j < d; ++j) {
         if (col[j] < 0 || col[j] >= t || lab[j] < 0) {
             set_error("gsi_join_step_noalloc: column out of range or negative label");

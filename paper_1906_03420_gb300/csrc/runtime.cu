@@ -11,6 +11,12 @@
 #include "internal.h"
 #include "runtime.h"
 
+int32_t gsi_graph::label_rank(int32_t label) const {
+    auto it = std::lower_bound(vlabels.begin(), vlabels.end(), label);
+    if (it == vlabels.end() || *it != label) return -1;
+    return (int32_t)(it - vlabels.begin());
+}
+
 namespace gsi {
 
 static thread_local std::string t_last_error;
@@ -152,7 +158,8 @@ void plan_order(const QueryGraph &q, const uint64_t *cand, const uint64_t *freq,
 }
 
 // JoinStep for position p (t = p columns), given the order and e0 choice.
-void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, std::vector<JoinStep> &steps) {
+void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, const int32_t *ranks,
+                std::vector<JoinStep> &steps) {
     const int k = q.k;
     int pos[GSI_MAX_QUERY_VERTICES];
     for (int p = 0; p < k; ++p) pos[order[p]] = p;
@@ -162,6 +169,7 @@ void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first,
         s.t = p;
         s.d = 0;
         int u = order[p];
+        s.ulab = ranks[u];
         s.col[s.d] = pos[first[p]];
         s.lab[s.d] = q.elab[u][first[p]];
         ++s.d;
@@ -377,6 +385,15 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         *out = res.release();
         return GSI_OK;
     }
+    // a query vertex label that no data vertex carries: no embeddings
+    int32_t ranks[GSI_MAX_QUERY_VERTICES];
+    for (int u = 0; u < q.k; ++u) {
+        ranks[u] = g->label_rank(q.vlab[u]);
+        if (ranks[u] < 0) {
+            *out = res.release();
+            return GSI_OK;
+        }
+    }
 
     QuerySig qs;
     query_signatures(q.vl.data(), q.k, q.src.data(), q.dst.data(), q.lab.data(), q.qm, &qs);
@@ -445,7 +462,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     }
     if (rc == GSI_OK && !empty) {
         for (int p = 0; p < q.k; ++p) x.order[p] = order[p];
-        make_steps(q, order, first, x.steps);
+        make_steps(q, order, first, ranks, x.steps);
         // seed: M = C(u_first) as a one-column table (Alg. 2)
         const uint64_t R0 = cand_h[order[0]];
         int32_t *M0 = nullptr;

@@ -72,7 +72,8 @@ gsi_status validate_query(const int32_t *qvlab, int32_t k, const int32_t *qsrc, 
                           const int32_t *qelab, int32_t qm, QueryGraph *q);
 void plan_order(const QueryGraph &q, const uint64_t *cand, const uint64_t *freq, int32_t nlabels, int32_t *order,
                 int32_t *first);
-void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, std::vector<JoinStep> &steps);
+void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, const int32_t *ranks,
+                std::vector<JoinStep> &steps);
 gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o, gsi_result **out);
 
 }  // namespace gsi

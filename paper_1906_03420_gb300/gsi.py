@@ -42,9 +42,9 @@ class c_graph_opts(ctypes.Structure):
 
 
 class c_graph_info(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32), ("n_elabels", ctypes.c_int32), ("m", ctypes.c_int64),
-                ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double),
-                ("off", ctypes.c_void_p), ("ci", ctypes.c_void_p), ("sig", ctypes.c_void_p)]
+    _fields_ = [("n", ctypes.c_int32), ("n_elabels", ctypes.c_int32), ("n_vlabels", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("device_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("off", ctypes.c_void_p), ("ci", ctypes.c_void_p), ("cl", ctypes.c_void_p), ("sig", ctypes.c_void_p)]
 
 
 class c_stats(ctypes.Structure):
@@ -115,7 +115,7 @@ def load(build_if_missing: bool = False):
     L.gsi_graph_destroy.restype = None
     L.gsi_graph_get_info.argtypes = [VP, ctypes.POINTER(c_graph_info)]
     L.gsi_graph_get_info.restype = st
-    L.gsi_graph_export.argtypes = [VP, VP, VP, VP]
+    L.gsi_graph_export.argtypes = [VP, VP, VP, VP, VP]
     L.gsi_graph_export.restype = st
     L.gsi_graph_label_freq.argtypes = [VP, U64P, ctypes.c_int32]
     L.gsi_graph_label_freq.restype = st
@@ -134,8 +134,8 @@ def load(build_if_missing: bool = False):
     L.gsi_filter.restype = st
     L.gsi_query_signatures.argtypes = [I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, U32P]
     L.gsi_query_signatures.restype = st
-    L.gsi_join_step.argtypes = [VP, VP, ctypes.c_uint64, ctypes.c_int32, VP, I32P, I32P, ctypes.c_int32, VP,
-                                ctypes.c_uint64, U64P, VP]
+    L.gsi_join_step.argtypes = [VP, VP, ctypes.c_uint64, ctypes.c_int32, VP, ctypes.c_int32, I32P, I32P,
+                                ctypes.c_int32, VP, ctypes.c_uint64, U64P, VP]
     L.gsi_join_step.restype = st
     L.gsi_join_step_noalloc.argtypes = L.gsi_join_step.argtypes
     L.gsi_join_step_noalloc.restype = st
@@ -287,15 +287,16 @@ class Graph:
         _check(load().gsi_graph_get_info(self._h, ctypes.byref(i)), "gsi_graph_get_info")
         return i
 
-    def export(self) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
-        """(off uint32[n*L+1], ci int32[2m], sig uint32[16, n]) copied to the host."""
+    def export(self) -> tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+        """(off uint32[n*L+1], ci int32[2m], cl uint16[2m], sig uint32[16, n]) copied to the host."""
         i = self.info()
         off = np.zeros(i.n * i.n_elabels + 1, np.uint32)
         ci = np.zeros(max(2 * i.m, 1), np.int32)
+        cl = np.zeros(max(2 * i.m, 1), np.uint16)
         sig = np.zeros((SIG_WORDS, i.n), np.uint32)
-        _check(load().gsi_graph_export(self._h, off.ctypes.data, ci.ctypes.data, sig.ctypes.data),
+        _check(load().gsi_graph_export(self._h, off.ctypes.data, ci.ctypes.data, cl.ctypes.data, sig.ctypes.data),
                "gsi_graph_export")
-        return off, ci[: 2 * i.m], sig
+        return off, ci[: 2 * i.m], cl[: 2 * i.m], sig
 
     def label_freq(self) -> np.ndarray:
         L = self.info().n_elabels
@@ -334,25 +335,25 @@ class Graph:
                                  bm.ctypes.data, cnt.ctypes.data, _stream_handle(stream)), "gsi_filter")
         return bm, cnt
 
-    def join_step(self, M_ptr: int, R: int, t: int, cand_ptr: int, cols, labs, out_ptr: int, out_cap: int,
-                  stream=None) -> int:
+    def join_step(self, M_ptr: int, R: int, t: int, cand_ptr: int, ulabel: int, cols, labs, out_ptr: int,
+                  out_cap: int, stream=None) -> int:
         """One join iteration on device buffers (pointers); returns the survivor count."""
         c = _i32(cols)
         l = _i32(labs)
         cnt = ctypes.c_uint64()
-        _check(load().gsi_join_step(self._h, M_ptr, R, t, cand_ptr, _p32(c), _p32(l), c.shape[0], out_ptr, out_cap,
-                                    ctypes.byref(cnt), _stream_handle(stream)), "gsi_join_step")
+        _check(load().gsi_join_step(self._h, M_ptr, R, t, cand_ptr, ulabel, _p32(c), _p32(l), c.shape[0], out_ptr,
+                                    out_cap, ctypes.byref(cnt), _stream_handle(stream)), "gsi_join_step")
         return int(cnt.value)
 
-    def join_step_noalloc(self, M_ptr: int, R: int, t: int, cand_ptr: int, cols, labs, out_ptr: int, out_cap: int,
-                          stream=None) -> int:
+    def join_step_noalloc(self, M_ptr: int, R: int, t: int, cand_ptr: int, ulabel: int, cols, labs, out_ptr: int,
+                          out_cap: int, stream=None) -> int:
         """join_step with the library's static scratch array: no device allocation
         (for callers that may not allocate); returns the survivor count."""
         c = _i32(cols)
         l = _i32(labs)
         cnt = ctypes.c_uint64()
-        _check(load().gsi_join_step_noalloc(self._h, M_ptr, R, t, cand_ptr, _p32(c), _p32(l), c.shape[0], out_ptr,
-                                            out_cap, ctypes.byref(cnt), _stream_handle(stream)),
+        _check(load().gsi_join_step_noalloc(self._h, M_ptr, R, t, cand_ptr, ulabel, _p32(c), _p32(l), c.shape[0],
+                                            out_ptr, out_cap, ctypes.byref(cnt), _stream_handle(stream)),
                "gsi_join_step_noalloc")
         return int(cnt.value)
 

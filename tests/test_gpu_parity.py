@@ -51,13 +51,16 @@ def rmat_graph(seed, scale, m, nvl, nel):
 
 # ------------------------------------------------------------------ layout
 def expected_layout(g, L):
+    """Entries sorted by (vertex, edge label, label rank of the neighbour, neighbour)."""
+    uniq = np.unique(g.vlab)
+    rank = np.searchsorted(uniq, g.vlab).astype(np.int64)
     v = np.concatenate([g.src, g.dst]).astype(np.int64)
     w = np.concatenate([g.dst, g.src]).astype(np.int64)
     l = np.concatenate([g.elab, g.elab]).astype(np.int64)
-    idx = np.lexsort((w, l, v))
+    idx = np.lexsort((w, rank[w], l, v))
     seg = v[idx] * L + l[idx]
     off = np.searchsorted(seg, np.arange(g.n * L + 1), side="left").astype(np.uint32)
-    return off, w[idx].astype(np.int32)
+    return off, w[idx].astype(np.int32), rank[w[idx]].astype(np.uint16)
 
 
 @pytest.mark.parametrize("case", ["random", "er1k", "rmat14", "isolated"])
@@ -75,10 +78,12 @@ def test_layout_matches_oracle_adjacency(pkg, case):
     info = G.info()
     L = int(g.elab.max()) + 1 if g.m else 1
     assert info.n == g.n and info.m == g.m and info.n_elabels == L
-    off, ci, sig = G.export()
-    eoff, eci = expected_layout(g, L)
+    off, ci, cl, sig = G.export()
+    eoff, eci, ecl = expected_layout(g, L)
+    assert info.n_vlabels == np.unique(g.vlab).shape[0]
     assert np.array_equal(off, eoff)
     assert np.array_equal(ci, eci)
+    assert np.array_equal(cl, ecl)
     assert np.array_equal(sig.T, oracle.data_signatures(og(g)))
     assert np.array_equal(G.label_freq(), np.bincount(g.elab, minlength=L).astype(np.uint64))
 
@@ -137,7 +142,7 @@ def _prefix_tables(O, g, q, order):
     return member, tables, steps
 
 
-def _gpu_step(pkg, G, M, member_u, cols, labs, out_cap=None):
+def _gpu_step(pkg, G, M, member_u, ulabel, cols, labs, out_cap=None):
     import torch
     t = M.shape[1]
     R = M.shape[0]
@@ -145,7 +150,7 @@ def _gpu_step(pkg, G, M, member_u, cols, labs, out_cap=None):
     cd = dev(bitmap_of(member_u).view(np.int32))
     cap = out_cap if out_cap is not None else max(1, R * 64)
     out = torch.full((max(cap, 1), t + 1), -7, dtype=torch.int32, device="cuda")
-    cnt = G.join_step(Md.data_ptr(), R, t, cd.data_ptr(), cols, labs, out.data_ptr(), cap)
+    cnt = G.join_step(Md.data_ptr(), R, t, cd.data_ptr(), int(ulabel), cols, labs, out.data_ptr(), cap)
     torch.cuda.synchronize()
     return cnt, out[: min(cnt, cap)].cpu().numpy()
 
@@ -171,7 +176,7 @@ def test_join_step_matches_oracle(pkg, seed):
             rot = int(rng.integers(0, len(cols)))
             cols_r = cols[rot:] + cols[:rot]
             labs_r = labs[rot:] + labs[:rot]
-            cnt, rows = _gpu_step(pkg, G, M, member[u], cols_r, labs_r)
+            cnt, rows = _gpu_step(pkg, G, M, member[u], q.vlab[u], cols_r, labs_r)
             want = tables[t]
             assert cnt == want.shape[0]
             assert np.array_equal(oracle.sort_rows(rows), want)
@@ -191,13 +196,13 @@ def test_join_step_skewed_hub(pkg):
     # rows: the hub first, then a ragged number of leaf rows
     M = np.concatenate([[0], np.arange(1, 3001, dtype=np.int32)]).astype(np.int32)[:, None]
     everyone = np.ones(n, bool)
-    cnt, rows = _gpu_step(pkg, G, M, everyone, [0], [0], out_cap=hub_deg + 10_000)
+    cnt, rows = _gpu_step(pkg, G, M, everyone, 0, [0], [0], out_cap=hub_deg + 10_000)
     want = oracle.join_step(O, M, everyone, [0], [0])
     assert cnt == want.shape[0]
     assert np.array_equal(oracle.sort_rows(rows), want)
     # two-column rows (hub, leaf) extended by a vertex adjacent to both (a triangle closer)
     M2 = want[want[:, 0] == 0][:5000]
-    cnt2, rows2 = _gpu_step(pkg, G, M2, everyone, [0, 1], [0, 0])
+    cnt2, rows2 = _gpu_step(pkg, G, M2, everyone, 0, [0, 1], [0, 0])
     want2 = oracle.join_step(O, M2, everyone, [0, 1], [0, 0])
     assert cnt2 == want2.shape[0] and np.array_equal(oracle.sort_rows(rows2), want2)
 
@@ -208,28 +213,30 @@ def test_join_step_edge_cases(pkg):
     O = og(g)
     everyone = np.ones(6, bool)
     # empty M
-    assert G.join_step(0, 0, 1, 0, [0], [0], 0, 0) == 0
-    # label beyond the graph's labels: no candidates
+    assert G.join_step(0, 0, 1, 0, 0, [0], [0], 0, 0) == 0
+    # edge label beyond the graph's labels, or a vertex label no vertex has: no candidates
     M = np.arange(6, dtype=np.int32)[:, None]
-    cnt, _ = _gpu_step(pkg, G, M, everyone, [0], [5])
+    cnt, _ = _gpu_step(pkg, G, M, everyone, 0, [0], [5])
+    assert cnt == 0
+    cnt, _ = _gpu_step(pkg, G, M, everyone, 3, [0], [0])
     assert cnt == 0
     # rows with repeated values (injectivity applies to every column)
     M = np.array([[0, 0], [1, 1], [2, 0]], np.int32)
-    cnt, rows = _gpu_step(pkg, G, M, everyone, [1], [0])
+    cnt, rows = _gpu_step(pkg, G, M, everyone, 0, [1], [0])
     want = oracle.join_step(O, M, everyone, [1], [0])
     assert cnt == want.shape[0] and np.array_equal(oracle.sort_rows(rows), want)
     # out_cap smaller than the count: count exact, rows valid and distinct
     M = np.repeat(np.arange(6, dtype=np.int32), 40)[:, None]
     full = oracle.join_step(O, M, everyone, [0], [0])
-    cnt, rows = _gpu_step(pkg, G, M, everyone, [0], [0], out_cap=7)
+    cnt, rows = _gpu_step(pkg, G, M, everyone, 0, [0], [0], out_cap=7)
     assert cnt == full.shape[0] and rows.shape[0] == 7
     fs = {tuple(r) for r in full}
     assert all(tuple(r) in fs for r in rows)
     # invalid arguments
     with pytest.raises(pkg.GsiError):
-        G.join_step(0, 1, 1, 0, [1], [0], 0, 0)     # column outside [0, t)
+        G.join_step(0, 1, 1, 0, 0, [1], [0], 0, 0)     # column outside [0, t)
     with pytest.raises(pkg.GsiError):
-        G.join_step(0, 1, 1, 0, [0, 0], [0, 0], 0, 0)   # d > t
+        G.join_step(0, 1, 1, 0, 0, [0, 0], [0, 0], 0, 0)   # d > t
 
 
 # ------------------------------------------------------------ full queries

@@ -36,13 +36,13 @@ def _bitmap(member):
     return np.packbits(padded, bitorder="little").view(np.uint32)
 
 
-def _run(G, fn, M, member_u, cols, labs, cap):
+def _run(G, fn, M, member_u, ulabel, cols, labs, cap):
     import torch
     t = M.shape[1]
     Md = torch.from_numpy(np.ascontiguousarray(M)).cuda()
     cd = torch.from_numpy(_bitmap(member_u).view(np.int32)).cuda()
     out = torch.full((cap, t + 1), -1, dtype=torch.int32, device="cuda")
-    cnt = fn(Md.data_ptr(), M.shape[0], t, cd.data_ptr(), cols, labs, out.data_ptr(), cap)
+    cnt = fn(Md.data_ptr(), M.shape[0], t, cd.data_ptr(), int(ulabel), cols, labs, out.data_ptr(), cap)
     torch.cuda.synchronize()
     return cnt, oracle.sort_rows(out[: min(cnt, cap)].cpu().numpy())
 
@@ -70,10 +70,10 @@ def test_noalloc_matches_allocating_join_step_twice(pkg):
             if M.shape[0] == 0 or M.shape[0] > 200_000:
                 break
             cap = max(16, 64 * M.shape[0])
-            want_n, want = _run(G, G.join_step, M, member[u], cols, labs, cap)
+            want_n, want = _run(G, G.join_step, M, member[u], q.vlab[u], cols, labs, cap)
             # two calls in a row on the shared static scratch
             for _ in range(2):
-                got_n, got = _run(G, G.join_step_noalloc, M, member[u], cols, labs, cap)
+                got_n, got = _run(G, G.join_step_noalloc, M, member[u], q.vlab[u], cols, labs, cap)
                 assert got_n == want_n
                 assert np.array_equal(got, want)
                 calls += 1
@@ -85,6 +85,6 @@ def test_noalloc_rejects_sizes_beyond_its_limit(pkg):
     g = H.complete(4)
     G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
     with pytest.raises(pkg.GsiError) as e:
-        G.join_step_noalloc(16, (1 << 20) + 1, 1, 16, [0], [0], 0, 0)
+        G.join_step_noalloc(16, (1 << 20) + 1, 1, 16, 0, [0], [0], 0, 0)
     assert e.value.status == pkg.GSI_EINVAL
     assert "2^20" in str(e.value)
