@@ -180,12 +180,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     row_cap = w.row_cap
+    budget = int(args.budget_gb * (1 << 30))
 
     def one_step(stats_list=None):
         total = 0
         for q in mine:
             st = pkg.c_stats() if stats_list is not None else None
-            r = G.query(q, stream=stream, row_cap=row_cap, stats=st)
+            r = G.query(q, stream=stream, row_cap=row_cap, stats=st, mem_budget=budget)
             total += r.count
             r.close()
             if st is not None:
@@ -228,6 +229,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     filter_ms = sum(s.filter_ms for s in stats)
     filter_bytes = sum(s.filter_bytes for s in stats)
     kernels = sum(s.kernels for s in stats)
+    host_driven = sum(s.host_driven for s in stats)
     allv = combine([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
                     float(join_launches), filter_ms, float(filter_bytes), float(kernels)], world, device="cuda")
     t_max_ms = float(allv[:, 0].max())
@@ -292,7 +294,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
            "config": cfg, "queries_per_s": tot_q / (t_max_ms * 1e-3) if t_max_ms > 0 else None,
            "embeddings_per_step": tot_emb / args.steps, "wall_s": wall, "roofline": roofline,
            "filter": {"achieved_gbs": fb / (fms * 1e-3) / 1e9 if fms > 0 else None, "ms_per_step": fms / args.steps},
-           "gpu_launches": int(allv[:, 8].sum()), "clocks": clocks, "e2e": e2e}
+           "gpu_launches": int(allv[:, 8].sum()), "host_driven_queries": int(host_driven), "clocks": clocks,
+           "e2e": e2e}
     if args.cpu_baseline and rank == 0:
         out["cpu_baseline"] = cpu_baseline(queries, g)
     return out
@@ -359,6 +362,7 @@ def main():
     ap.add_argument("--workload", default="medium")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--queries", default="", help="subset of query indices ('3,5,8' or 'a:b'); default all")
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="per-query device memory budget (0 = library default)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -121,6 +121,8 @@ typedef struct {
     uint64_t tiles;          /* row ranges processed (memory-bounded splits) */
     uint64_t peak_bytes;     /* peak intermediate-table bytes */
     uint64_t kernels;        /* kernels launched by this library */
+    uint64_t host_driven;    /* queries run host-driven (requested or after an
+                                arena overflow) */
     uint64_t cand[GSI_MAX_QUERY_VERTICES];   /* |C(u)| per query vertex */
     int32_t order[GSI_MAX_QUERY_VERTICES];   /* join order (query vertex ids) */
     int32_t k;
@@ -132,19 +134,26 @@ typedef struct {
     void *stream;            /* stream for all device work of the query */
     uint64_t row_cap;        /* max embeddings materialised; 0 = no cap.  The
                                 count stays exact beyond the cap. */
-    uint64_t mem_budget;     /* bytes for intermediate tables; 0 = half of the
-                                device's free memory at call time */
+    uint64_t mem_budget;     /* bytes for intermediate tables; 0 = 40% of the
+                                device's memory */
     int32_t count_only;      /* 1: count embeddings, materialise none */
     int32_t semantics;       /* GSI_ISOMORPHISM */
     const int32_t *order;    /* optional join order (k query vertex ids, each
                                 connected to an earlier one); NULL = Alg. 2 */
     gsi_stats *stats;        /* optional: timing and work counters */
+    int32_t host_driven;     /* 1: size every step on the host and split row
+                                ranges to fit the budget (the path otherwise
+                                taken only when the device-driven arena
+                                overflows) */
 } gsi_query_opts;
 
 /*
  * Find all embeddings of Q in G (Defs. 2-3): filter (Sec. III-A), order by
  * Alg. 2, then one join iteration per remaining query vertex (Alg. 3 with the
- * Alg. 4 upper bound on each row's output).
+ * Alg. 4 upper bound on each row's output).  The steps run device-driven in
+ * an arena of mem_budget bytes (one scratch and two table regions, sizes
+ * kept on the device, no host wait between steps); if a table does not fit,
+ * the query is redone host-driven with row ranges halved until each fits.
  *   qvlab int32[k]; query edges {qsrc[i], qdst[i]} with label qelab[i], i < qm.
  * Q must be connected (the paper assumes so, Sec. II-A), have 1 <= k <= 32
  * vertices, no self-loop and no repeated vertex pair: otherwise GSI_EINVAL.

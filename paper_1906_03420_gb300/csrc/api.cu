@@ -274,14 +274,10 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
     if (R == 0 || empty) return GSI_OK;
     GSI_TRY(prepare_device(g->device));
     cudaStream_t st = (cudaStream_t)stream;
-    uint64_t *F = nullptr, *scr = nullptr, *h = nullptr;
+    uint64_t *F = nullptr, *scr = nullptr;
+    uint64_t h[2] = {0, 0};
     int64_t *part = nullptr;
     unsigned long long *d_cnt = nullptr;
-    GSI_CUDA_TRY(cudaMallocHost(&h, 16));
-    struct HostGuard {
-        uint64_t *p;
-        ~HostGuard() { cudaFreeHost(p); }
-    } hg{h};
     GSI_CUDA_TRY(cudaMallocAsync(&F, 8 * (R + 1), st));
     GSI_CUDA_TRY(cudaMallocAsync(&scr, 8 * (uint64_t)join_scan_scratch(R), st));
     GSI_CUDA_TRY(cudaMallocAsync(&d_cnt, 8, st));

@@ -83,4 +83,42 @@ gsi_status launch_join(const gsi_graph *g, const int32_t *M, uint64_t R, const J
                        unsigned long long *out_count, int count_only, unsigned long long *stats, cudaStream_t st);
 inline uint64_t join_tiles(uint64_t total) { return (total + JOIN_NV - 1) / JOIN_NV; }
 
+// One join step of a cooperative query launch (see join.cu): the host sets
+// the regions, the device the sizes.
+struct DStep {
+    // set by the host
+    const int32_t *M;                  // input table (t columns)
+    int32_t *out;                      // output table region
+    uint64_t out_bytes;                // bytes of the output region
+    uint64_t row_cap;                  // output rows allowed (0 = no limit)
+    uint64_t *S;                       // scratch region: F and part at the front, caps at the back
+    uint64_t S_words;
+    int32_t t, count_only;
+    // set on the device
+    unsigned long long count;          // survivors (exact even past out_cap); [0]: seed size
+    unsigned long long next_tile;
+    uint64_t R, total, ntiles, out_cap;
+};
+
+// Grid-barrier and status words of one cooperative query launch.
+struct QueryCtl {
+    unsigned bar_count, bar_gen;
+    unsigned fail;        // 1 scratch too small, 2 table overflow, 4 barrier wait gave up
+    unsigned pad;
+};
+constexpr int QUERY_MAX_CTAS = 1024;
+size_t join_args_size();
+// Seed + every join step of one query in one cooperative launch.  cfg_dev:
+// join_args_size() * k bytes; dsteps: k records (host-initialised static
+// fields); bsum: QUERY_MAX_CTAS words.  steps[0].count receives |seed|.
+gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
+                             const int32_t *order, int count_only, unsigned long long *stats, void *cfg_dev,
+                             DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out,
+                             cudaStream_t stream);
+// fail bits: 1 = scratch region too small, 2 = a table overflowed its region.
+gsi_status launch_step_device(const gsi_graph *g, const JoinStep &s, DStep *st, unsigned *fail, const uint32_t *cand,
+                              int count_only, unsigned long long *stats, cudaStream_t stream);
+gsi_status launch_join_device(const gsi_graph *g, const JoinStep &s, DStep *st, unsigned *fail, const uint32_t *cand,
+                              int count_only, unsigned long long *stats, cudaStream_t stream);
+
 }  // namespace gsi

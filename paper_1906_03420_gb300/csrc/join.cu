@@ -35,6 +35,10 @@
 //   * survivors are compacted with one block-wide prefix sum and one global
 //     atomic per CTA, then written once as rows of M' (Prealloc-Combine: the
 //     join runs once; the output buffer is sized by F's total).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "internal.h"
 #include "scan.cuh"
 
@@ -100,6 +104,7 @@ struct CapLoadProducer {
     uint64_t W;
     __device__ uint64_t operator()(int64_t i) const { return (uint64_t)caps[i] + W; }
 };
+
 
 template <typename P1, typename P2, typename Wr>
 cudaError_t two_producer_scan(P1 p1, P2 p2, int64_t n, Wr write, uint64_t *scratch, cudaStream_t st) {
@@ -174,8 +179,15 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
     return r;
 }
 
+// One tile of NV candidate slots.  The table-dependent inputs (M, R, F,
+// total, part, out, out_cap, out_count) are arguments so that the same code
+// serves host-sized launches (one CTA per tile) and device-sized persistent
+// launches (CTAs take tiles from a counter).
 template <int NT, int VT>
-__global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a) {
+__device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *__restrict__ M, int64_t R,
+                                          const uint64_t *__restrict__ F, uint64_t total,
+                                          const int64_t *__restrict__ part, int32_t *__restrict__ out,
+                                          uint64_t out_cap, unsigned long long *out_count, uint64_t tile) {
     constexpr int NV = NT * VT;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long wt[NT / 32];
@@ -191,19 +203,19 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
     uint32_t *lst = base0 + a.rmax;                                     // rmax * 2 * dm1
     int32_t *rowv = reinterpret_cast<int32_t *>(lst + (size_t)a.rmax * 2 * dm1);   // rmax * t
 
-    const uint64_t s0 = (uint64_t)blockIdx.x * NV;
-    const uint64_t s1 = min(s0 + (uint64_t)NV, a.total);
-    const int64_t r_lo = a.part[blockIdx.x];
-    const int64_t r_hi = min(a.part[blockIdx.x + 1], a.R - 1);
+    const uint64_t s0 = tile * NV;
+    const uint64_t s1 = min(s0 + (uint64_t)NV, total);
+    const int64_t r_lo = part[tile];
+    const int64_t r_hi = min(part[tile + 1], R - 1);
     const int nr = (int)(r_hi - r_lo + 1);
 
     // ---- stage the tile's rows: values, candidate sub-list, other sub-lists
     for (int x = threadIdx.x; x < NV; x += NT) rowmap[x] = 0;
-    for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = a.F[r_lo + lr];
+    for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = F[r_lo + lr];
     __syncthreads();
     unsigned long long bytes = 0;
     for (int lr = threadIdx.x; lr < nr; lr += NT) {
-        const int32_t *row = a.M + (r_lo + lr) * (int64_t)t;
+        const int32_t *row = M + (r_lo + lr) * (int64_t)t;
         int32_t *rv = rowv + lr * t;
         for (int c = 0; c < t; ++c) rv[c] = row[c];
         // the row's lists: the shortest label sub-list supplies candidates
@@ -307,17 +319,17 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
             run += c;
         }
         wcnt[NT / 32] = run;
-        gbase_s = run ? atomicAdd(a.out_count, (unsigned long long)run) : 0ull;
+        gbase_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
     }
     __syncthreads();
     const unsigned nsurv = wcnt[NT / 32];
     if (!a.count_only && nw > 0) {
         const uint64_t base = gbase_s + wcnt[warp];
-        const uint64_t room = a.out_cap > base ? a.out_cap - base : 0;
+        const uint64_t room = out_cap > base ? out_cap - base : 0;
         const unsigned nrow = (unsigned)min((uint64_t)nw, room);
         const int W1 = t + 1;
         const unsigned nel = nrow * (unsigned)W1;
-        int32_t *dst = a.out + base * (uint64_t)W1;
+        int32_t *dst = out + base * (uint64_t)W1;
         int row = lane / W1, colx = lane % W1;
         const int qrow = 32 / W1, qcol = 32 % W1;
         for (unsigned e = lane; e < nel; e += 32) {
@@ -338,6 +350,192 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
             atomicAdd(a.stats, bsum);
             atomicAdd(a.stats + 1, isum);
         }
+    }
+}
+
+template <int NT, int VT>
+__global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a) {
+    join_tile<NT, VT>(a, a.M, a.R, a.F, a.total, a.part, a.out, a.out_cap, a.out_count, blockIdx.x);
+}
+
+// ------------------------------------------------- one launch per query
+// The whole join of one query in a single cooperative launch: the seed, then
+// for every step the bound scan, the tile partition and the join tiles, with
+// a grid barrier between phases.  All CTAs are co-resident (cooperative
+// launch), so the barrier is a counter and a generation word; every wait is
+// bounded, and a CTA that gives up sets an error bit and returns, as does
+// every CTA that later sees the bit, so the kernel always terminates.
+
+constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 24;   // x ~64 ns sleeps: about a second
+
+__device__ __forceinline__ bool grid_barrier(QueryCtl *ctl, unsigned nblocks) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ctl->bar_gen;
+        volatile unsigned *fail = &ctl->fail;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == g) {
+                if (*fail & 4u) { ok = 0; break; }
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    atomicOr(&ctl->fail, 4u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok && !(*fail & 4u);
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Sum of v over this CTA's predecessors (j < blockIdx.x) and over all CTAs.
+__device__ __forceinline__ void cta_prefix(const unsigned long long *bsum, unsigned nblocks, unsigned long long *wt,
+                                           unsigned long long *pre, unsigned long long *tot) {
+    unsigned long long p = 0, q = 0;
+    for (unsigned j = threadIdx.x; j < nblocks; j += blockDim.x) {
+        const unsigned long long v = bsum[j];
+        q += v;
+        if (j < blockIdx.x) p += v;
+    }
+    *pre = block_sum<JOIN_NT, unsigned long long>(p, wt);
+    *tot = block_sum<JOIN_NT, unsigned long long>(q, wt);
+}
+
+template <int NT, int VT>
+__global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs, DStep *steps, int k, QueryCtl *ctl,
+                                              const uint32_t *__restrict__ seed_bitmap, int64_t nwords,
+                                              unsigned long long *bsum) {
+    constexpr int NV = NT * VT;
+    __shared__ unsigned long long wt[NT / 32];
+    __shared__ unsigned long long tile_s;
+    const unsigned G = gridDim.x;
+    const uint64_t W = (uint64_t)JOIN_ROW_WEIGHT;
+    unsigned long long pre, tot;
+
+    // ---- seed: C(u_first) as the one-column table in the first region (Alg. 2)
+    int32_t *seed_out = const_cast<int32_t *>(steps[1].M);
+    {
+        const uint64_t per = ((uint64_t)nwords + G - 1) / G;
+        const uint64_t chunk = (per + SCAN_NV - 1) / SCAN_NV * SCAN_NV;
+        const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min((uint64_t)nwords, lo + chunk);
+        unsigned long long c = 0;
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += NT) c += __popc(seed_bitmap[i]);
+        c = block_sum<NT, unsigned long long>(c, wt);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = c;
+        if (!grid_barrier(ctl, G)) return;
+        cta_prefix(bsum, G, wt, &pre, &tot);
+        unsigned long long run = pre;
+        for (uint64_t base = lo; base < hi; base += NT) {
+            const uint64_t i = base + threadIdx.x;
+            const uint32_t b = i < hi ? seed_bitmap[i] : 0u;
+            unsigned long long t2;
+            unsigned long long pos = block_exclusive_scan<NT, unsigned long long>(__popc(b), wt, &t2) + run;
+            uint32_t x = b;
+            while (x) {
+                seed_out[pos++] = (int32_t)(i * 32 + (uint64_t)(__ffs(x) - 1));
+                x &= x - 1;
+            }
+            run += t2;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) steps[0].count = tot;
+        if (!grid_barrier(ctl, G)) return;
+    }
+
+    for (int t = 1; t < k; ++t) {
+        DStep *st = steps + t;
+        const JoinArgs &a = cfgs[t];
+        const uint64_t R = steps[t - 1].count;
+        // the previous table must have fit its region; the scratch must fit too
+        if (t > 1 && steps[t - 1].count > steps[t - 1].out_cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 2u);
+            return;
+        }
+        if ((R + 1) * 8 + R * 4 + 64 > st->S_words * 8) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
+            return;
+        }
+        uint64_t *F = st->S;
+        uint32_t *caps = reinterpret_cast<uint32_t *>(st->S + st->S_words) - R;
+        const int32_t *M = st->M;
+        // phase 1: each row's bound (the shortest label sub-list), per-CTA sums
+        const uint64_t per = (R + G - 1) / G;
+        const uint64_t chunk = (per + SCAN_NV - 1) / SCAN_NV * SCAN_NV;
+        const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(R, lo + chunk);
+        unsigned long long sum = 0, sbytes = 0;
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += NT) {
+            uint32_t c = row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl);
+            caps[i] = c;
+            sum += (unsigned long long)c + W;
+        }
+        sum = block_sum<NT, unsigned long long>(sum, wt);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = sum;
+        if (!grid_barrier(ctl, G)) return;
+        // phase 2: slot offsets F (each CTA rescans its own chunk)
+        cta_prefix(bsum, G, wt, &pre, &tot);
+        const uint64_t total = tot;
+        const uint64_t ntiles = (total + NV - 1) / NV;
+        int64_t *part = reinterpret_cast<int64_t *>(st->S + R + 1);
+        uint64_t cap = st->out_bytes / (4ull * (uint64_t)(t + 1));
+        if (st->row_cap && st->row_cap < cap) cap = st->row_cap;
+        if (st->count_only) cap = 0;
+        if ((R + 1 + ntiles + 1) * 8 + R * 4 + 64 > st->S_words * 8) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
+            return;
+        }
+        {
+            unsigned long long run = pre;
+            for (uint64_t base = lo; base < hi; base += NT) {
+                const uint64_t i = base + threadIdx.x;
+                const unsigned long long v = i < hi ? (unsigned long long)caps[i] + W : 0ull;
+                unsigned long long t2;
+                const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(v, wt, &t2) + run;
+                if (i < hi) F[i] = ex;
+                run += t2;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            F[R] = total;
+            st->R = R;
+            st->total = total;
+            st->ntiles = ntiles;
+            st->out_cap = cap;
+            if (a.stats) atomicAdd(a.stats, (unsigned long long)R * (4ull * a.s.d + 8ull * a.s.d + 8ull));
+        }
+        if (!grid_barrier(ctl, G)) return;
+        // phase 3: first row of every tile
+        for (uint64_t b = (uint64_t)blockIdx.x * NT + threadIdx.x; b <= ntiles; b += (uint64_t)G * NT) {
+            const uint64_t sl = min(b * (uint64_t)NV, total);
+            int64_t l2 = 0, h2 = (int64_t)R;
+            while (l2 < h2) {
+                int64_t mid = (l2 + h2 + 1) >> 1;
+                if (F[mid] <= sl) l2 = mid;
+                else h2 = mid - 1;
+            }
+            part[b] = l2;
+        }
+        if (!grid_barrier(ctl, G)) return;
+        // phase 4: the join tiles, taken from a counter
+        for (;;) {
+            if (threadIdx.x == 0) tile_s = atomicAdd(&st->next_tile, 1ull);
+            __syncthreads();
+            const uint64_t tile = tile_s;
+            if (tile >= ntiles) break;
+            join_tile<NT, VT>(a, M, (int64_t)R, F, total, part, st->out, cap, &st->count, tile);
+        }
+        if (!grid_barrier(ctl, G)) return;
     }
 }
 
@@ -419,6 +617,69 @@ gsi_status launch_join(const gsi_graph *g, const int32_t *M, uint64_t R, const J
     }
     k_join<JOIN_NT, JOIN_VT><<<(unsigned)ntiles, JOIN_NT, sm, st>>>(a);
     GSI_CUDA_TRY(cudaGetLastError());
+    return GSI_OK;
+}
+
+JoinArgs make_join_args(const gsi_graph *g, const JoinStep &s, const uint32_t *cand, int count_only,
+                        unsigned long long *stats) {
+    JoinArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.off = g->off; a.ci = g->ci; a.cl = g->cl; a.cand = cand;
+    a.stats = stats;
+    a.W = JOIN_ROW_WEIGHT;
+    a.rmax = JOIN_NV / JOIN_ROW_WEIGHT + 2;
+    a.count_only = count_only;
+    a.s = step_dev(g, s);
+    for (int i = 0; i <= GSI_MAX_QUERY_VERTICES; ++i) a.iperm[i] = i;
+    for (int c = 0; c <= s.t; ++c) a.iperm[s.perm[c]] = c;
+    return a;
+}
+
+size_t join_args_size() { return sizeof(JoinArgs); }
+
+gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
+                             const int32_t *order, int count_only, unsigned long long *stats, void *cfg_dev,
+                             DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out, cudaStream_t st) {
+    // per-step configuration, uploaded next to the step records
+    std::vector<JoinArgs> cfg((size_t)k);
+    size_t sm = 0;
+    for (int t = 1; t < k; ++t) {
+        const int co = (t == k - 1) && count_only;
+        cfg[t] = make_join_args(g, steps[t], bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords, co, stats);
+        sm = std::max(sm, join_smem(cfg[t].rmax, steps[t].t, steps[t].d));
+    }
+    if (sm > 200 * 1024) {
+        set_error("join: shared memory need exceeds 200 KB");
+        return GSI_EINVAL;
+    }
+    GSI_CUDA_TRY(cudaMemcpyAsync(cfg_dev, cfg.data(), sizeof(JoinArgs) * (size_t)k, cudaMemcpyHostToDevice, st));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static int attr_set[64];
+    static int nsm[64];
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        GSI_CUDA_TRY(cudaFuncSetAttribute(k_query<JOIN_NT, JOIN_VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024));
+        GSI_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
+        attr_set[dev] = 1;
+    }
+    int per_sm = 0;
+    GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<JOIN_NT, JOIN_VT>, JOIN_NT, sm));
+    if (per_sm < 1) {
+        set_error("join: the query kernel does not fit on an SM");
+        return GSI_EINVAL;
+    }
+    if (per_sm > 4) per_sm = 4;
+    int grid = (dev >= 0 && dev < 64 ? nsm[dev] : 152) * per_sm;
+    if (grid > QUERY_MAX_CTAS) grid = QUERY_MAX_CTAS;
+    *grid_out = grid;
+    const JoinArgs *cfgp = static_cast<const JoinArgs *>(cfg_dev);
+    const uint32_t *seed_bm = bitmaps + (uint64_t)order[0] * (uint64_t)g->nwords;
+    int64_t nwords = g->nwords;
+    void *args[] = {(void *)&cfgp, (void *)&dsteps, (void *)&k, (void *)&ctl, (void *)&seed_bm, (void *)&nwords,
+                    (void *)&bsum};
+    GSI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_query<JOIN_NT, JOIN_VT>, dim3(grid), dim3(JOIN_NT), args,
+                                             sm, st));
     return GSI_OK;
 }
 

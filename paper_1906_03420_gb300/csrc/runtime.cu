@@ -185,12 +185,27 @@ void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first,
 }
 
 // -------------------------------------------------------------- timing
+// Events are recycled through a per-thread pool: creating and destroying two
+// events per launch would cost more host time than the launches themselves.
+static thread_local std::vector<cudaEvent_t> t_event_pool;
+
+static cudaEvent_t pooled_event() {
+    if (!t_event_pool.empty()) {
+        cudaEvent_t e = t_event_pool.back();
+        t_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
 void Timer::begin(int kind) {
     if (!on) return;
     Rec r;
     r.kind = kind;
-    cudaEventCreate(&r.a);
-    cudaEventCreate(&r.b);
+    r.a = pooled_event();
+    r.b = pooled_event();
     cudaEventRecord(r.a, st);
     recs.push_back(r);
 }
@@ -207,8 +222,8 @@ void Timer::resolve(gsi_stats *s) {
             else if (r.kind == 1) { s->join_ms += ms; s->join_launches++; }
             else { s->other_ms += ms; s->other_launches++; }
         }
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
+        t_event_pool.push_back(r.a);
+        t_event_pool.push_back(r.b);
     }
     recs.clear();
 }
@@ -348,6 +363,134 @@ gsi_status Exec::run(int t, const int32_t *M, uint64_t R) {
     return rc;
 }
 
+
+// Device-driven execution of the whole join: one arena per query (a scratch
+// region and two table regions used in turn), every step's sizes computed on
+// the device, no host wait until the end.  The final table's region is handed
+// to the result when it is well used, or its rows are copied to a tight buffer.
+gsi_status Exec::run_device(bool *overflow) {
+    *overflow = false;
+    const uint64_t B = budget;
+    const uint64_t align = 256;
+    const uint64_t s_bytes = (B / 5) / align * align;
+    const uint64_t t_bytes = ((B - s_bytes) / 2) / align * align;
+    if (s_bytes < (1 << 16) || t_bytes < (uint64_t)g->n * 4 + 1024) {
+        *overflow = true;
+        return GSI_OK;
+    }
+    uint64_t *S = nullptr;
+    int32_t *reg[2] = {nullptr, nullptr};
+    unsigned char *ctl = nullptr;
+    const size_t ctl_bytes = (join_args_size() * (size_t)k + 255) / 256 * 256 +
+                             (sizeof(DStep) * (size_t)k + 255) / 256 * 256 + 256 + 8 * (size_t)QUERY_MAX_CTAS;
+    gsi_status rc = dalloc(*this, (void **)&S, s_bytes);
+    if (rc == GSI_OK) rc = dalloc(*this, (void **)&reg[0], t_bytes);
+    if (rc == GSI_OK) rc = dalloc(*this, (void **)&reg[1], t_bytes);
+    if (rc == GSI_OK) rc = dalloc(*this, (void **)&ctl, ctl_bytes);
+    auto release = [&]() {
+        if (S) cudaFreeAsync(S, st);
+        if (reg[0]) cudaFreeAsync(reg[0], st);
+        if (reg[1]) cudaFreeAsync(reg[1], st);
+        if (ctl) cudaFreeAsync(ctl, st);
+    };
+    if (rc != GSI_OK) {
+        release();
+        (void)cudaGetLastError();
+        *overflow = true;              // could not reserve the arena: use the splitting path
+        return GSI_OK;
+    }
+    peak = std::max(peak, s_bytes + 2 * t_bytes);
+    // control block: [step configs][step records][barrier/status][per-CTA sums]
+    unsigned char *p = ctl;
+    void *cfg_dev = p;
+    p += (join_args_size() * (size_t)k + 255) / 256 * 256;
+    DStep *dst = reinterpret_cast<DStep *>(p);
+    p += (sizeof(DStep) * (size_t)k + 255) / 256 * 256;
+    QueryCtl *qc = reinterpret_cast<QueryCtl *>(p);
+    p += 256;
+    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(p);
+    std::vector<DStep> hs((size_t)k);
+    std::memset(hs.data(), 0, sizeof(DStep) * (size_t)k);
+    for (int t = 1; t < k; ++t) {
+        DStep &h = hs[t];
+        h.M = reg[(t - 1) & 1];
+        h.out = reg[t & 1];
+        h.out_bytes = t_bytes;
+        const bool last = t == k - 1;
+        h.row_cap = last ? row_cap : 0;
+        h.count_only = last ? count_only : 0;
+        h.S = S;
+        h.S_words = s_bytes / 8;
+        h.t = t;
+    }
+    rc = GSI_OK;
+    if (cudaMemcpyAsync(dst, hs.data(), sizeof(DStep) * (size_t)k, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(qc, 0, sizeof(QueryCtl), st) != cudaSuccess) {
+        set_error("device-driven join: control upload failed");
+        rc = GSI_ECUDA;
+    }
+    unsigned long long *jstats = stats ? d_scalars + 1 : nullptr;
+    int grid = 0;
+    if (rc == GSI_OK) {
+        tm.begin(1);
+        rc = launch_query_coop(g, steps, k, bitmaps, order, count_only, jstats, cfg_dev, dst, qc, bsum, &grid, st);
+        tm.end();
+        kernels += 1;
+        tiles += (uint64_t)(k - 1);
+    }
+    // read back: status, and the final count / capacity
+    uint64_t fin[3] = {0, 0, 0};
+    if (rc == GSI_OK) {
+        if (cudaMemcpyAsync(h_pinned, &qc->fail, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(h_pinned + 1, &dst[k - 1].count, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(h_pinned + 2, &dst[k - 1].out_cap, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("device-driven join: kernel or readback failed");
+            rc = GSI_ECUDA;
+        }
+        fin[0] = h_pinned[0] & 0xffffffffu;
+        fin[1] = h_pinned[1];
+        fin[2] = h_pinned[2];
+    }
+    if (rc == GSI_OK && (fin[0] & 4u)) {
+        release();
+        set_error("device-driven join: a grid barrier wait ran past its limit");
+        return GSI_ETIMEOUT;
+    }
+    if (rc != GSI_OK || fin[0] != 0) {
+        release();
+        if (rc == GSI_OK) *overflow = true;
+        return rc;
+    }
+    const uint64_t count = fin[1];
+    const uint64_t rows = std::min(count, fin[2]);
+    int32_t *final_reg = reg[(k - 1) & 1];
+    res->count += count;
+    if (rows > 0) {
+        const uint64_t bytes = rows * (uint64_t)k * 4;
+        if (bytes * 4 >= t_bytes) {
+            res->chunks.push_back({final_reg, rows});      // the result keeps the region
+            res->materialised += rows;
+            reg[(k - 1) & 1] = nullptr;
+        } else {
+            int32_t *tight = nullptr;
+            rc = dalloc(*this, (void **)&tight, bytes);
+            if (rc == GSI_OK && cudaMemcpyAsync(tight, final_reg, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                set_error("device-driven join: result copy failed");
+                rc = GSI_ECUDA;
+            }
+            if (rc == GSI_OK) {
+                res->chunks.push_back({tight, rows});
+                res->materialised += rows;
+            } else if (tight) {
+                cudaFreeAsync(tight, st);
+            }
+        }
+    }
+    release();
+    return rc;
+}
+
 const uint32_t *Exec::cand(const JoinStep &s, int t) const {
     (void)s;
     return bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords;
@@ -371,9 +514,11 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     if (o.mem_budget) {
         x.budget = o.mem_budget;
     } else {
+        // a fixed share of the device (not of the momentarily free memory, which
+        // excludes blocks the stream-ordered pool keeps cached for reuse)
         size_t fr = 0, totm = 0;
         GSI_CUDA_TRY(cudaMemGetInfo(&fr, &totm));
-        x.budget = fr / 2;
+        x.budget = (uint64_t)(0.4 * (double)totm);
     }
     // a query edge label that no data edge carries: no embeddings
     for (int e = 0; e < q.qm; ++e)
@@ -398,11 +543,11 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     QuerySig qs;
     query_signatures(q.vl.data(), q.k, q.src.data(), q.dst.data(), q.lab.data(), q.qm, &qs);
     const uint64_t bm_words = (uint64_t)q.k * (uint64_t)g->nwords;
-    GSI_CUDA_TRY(cudaMallocHost(&x.h_pinned, 8 * (GSI_MAX_QUERY_VERTICES + 8)));
-    struct PinnedGuard {
-        Exec &x;
-        ~PinnedGuard() { cudaFreeHost(x.h_pinned); }
-    } pg{x};
+    // per-thread pinned staging for small readbacks (cudaFreeHost would
+    // synchronise the whole device, so the buffer lives as long as the thread)
+    static thread_local uint64_t *t_pinned = nullptr;
+    if (!t_pinned) GSI_CUDA_TRY(cudaMallocHost(&t_pinned, 8 * (GSI_MAX_QUERY_VERTICES + 8)));
+    x.h_pinned = t_pinned;
     unsigned long long *d_counts = nullptr;
     GSI_TRY(dalloc(x, (void **)&x.bitmaps, bm_words * 4));
     GSI_TRY(dalloc(x, (void **)&d_counts, 8 * GSI_MAX_QUERY_VERTICES + 32));
@@ -463,31 +608,36 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     if (rc == GSI_OK && !empty) {
         for (int p = 0; p < q.k; ++p) x.order[p] = order[p];
         make_steps(q, order, first, ranks, x.steps);
-        // seed: M = C(u_first) as a one-column table (Alg. 2)
+        // device-driven path first; the host-driven splitting path on overflow
+        bool overflow = true;
+        if (!o.host_driven && q.k > 1) rc = x.run_device(&overflow);
+        x.fell_back = overflow;
         const uint64_t R0 = cand_h[order[0]];
         int32_t *M0 = nullptr;
-        uint32_t *sscr = nullptr;
-        rc = dalloc(x, (void **)&M0, R0 * 4);
-        if (rc == GSI_OK) rc = dalloc(x, (void **)&sscr, 4 * (uint64_t)seed_scratch_words(g));
-        if (rc == GSI_OK) {
-            x.tm.begin(2);
-            rc = launch_seed(g, x.bitmaps + (uint64_t)order[0] * g->nwords, M0, sscr, x.st);
-            x.tm.end();
-            x.kernels += 3;
-        }
-        if (sscr) cudaFreeAsync(sscr, x.st);
-        if (rc == GSI_OK) {
-            x.live = R0 * 4;
-            x.peak = x.live;
-            if (q.k == 1) {
-                res->count = R0;
-                uint64_t keep = x.count_only ? 0 : (x.row_cap ? std::min(R0, x.row_cap) : R0);
-                if (keep) {
-                    rc = x.add_chunk(M0, keep, R0);
-                    M0 = nullptr;
+        if (rc == GSI_OK && overflow) {
+            // seed: M = C(u_first) as a one-column table (Alg. 2)
+            uint32_t *sscr = nullptr;
+            rc = dalloc(x, (void **)&M0, R0 * 4);
+            if (rc == GSI_OK) rc = dalloc(x, (void **)&sscr, 4 * (uint64_t)seed_scratch_words(g));
+            if (rc == GSI_OK) {
+                x.tm.begin(2);
+                rc = launch_seed(g, x.bitmaps + (uint64_t)order[0] * g->nwords, M0, sscr, x.st);
+                x.tm.end();
+                x.kernels += 3;
+            }
+            if (sscr) cudaFreeAsync(sscr, x.st);
+            if (rc == GSI_OK) {
+                x.live = R0 * 4;
+                if (q.k == 1) {
+                    res->count = R0;
+                    uint64_t keep = x.count_only ? 0 : (x.row_cap ? std::min(R0, x.row_cap) : R0);
+                    if (keep) {
+                        rc = x.add_chunk(M0, keep, R0);
+                        M0 = nullptr;
+                    }
+                } else {
+                    rc = x.run(1, M0, R0);
                 }
-            } else {
-                rc = x.run(1, M0, R0);
             }
         }
         if (M0) cudaFreeAsync(M0, x.st);
@@ -519,6 +669,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         s->join_bytes += x.join_bytes;
         s->join_items += x.join_items;
         s->kernels += x.kernels;
+        s->host_driven += (rc == GSI_OK && !empty && x.fell_back) ? 1 : 0;
     }
     if (rc != GSI_OK) return rc;
     *out = res.release();

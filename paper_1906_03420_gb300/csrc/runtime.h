@@ -57,12 +57,16 @@ struct Exec {
     uint64_t row_cap = 0;
     int count_only = 0;
     uint64_t join_bytes = 0, join_items = 0;
-    uint64_t kernels = 0;            // kernels launched (scan = 3, partition, join, filter, seed = 3)
+    uint64_t kernels = 0;
+    bool fell_back = false;          // the query ran host-driven            // kernels launched (scan = 3, partition, join, filter, seed = 3)
     gsi_result *res = nullptr;
     gsi_stats *stats = nullptr;
     Timer tm;
 
     gsi_status run(int t, const int32_t *M, uint64_t R);
+    // All steps enqueued with device-resident sizes; *overflow is set when a
+    // table or the scratch did not fit its region (nothing is added to res).
+    gsi_status run_device(bool *overflow);
     gsi_status add_chunk(int32_t *rows, uint64_t nrows, uint64_t alloc_rows);
     const uint32_t *cand(const JoinStep &s, int t) const;
 };

@@ -52,7 +52,8 @@ class c_stats(ctypes.Structure):
                 ("filter_launches", ctypes.c_uint64), ("join_launches", ctypes.c_uint64),
                 ("other_launches", ctypes.c_uint64), ("filter_bytes", ctypes.c_uint64),
                 ("join_bytes", ctypes.c_uint64), ("join_items", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
-                ("peak_bytes", ctypes.c_uint64), ("kernels", ctypes.c_uint64), ("cand", ctypes.c_uint64 * 32), ("order", ctypes.c_int32 * 32),
+                ("peak_bytes", ctypes.c_uint64), ("kernels", ctypes.c_uint64), ("host_driven", ctypes.c_uint64),
+                ("cand", ctypes.c_uint64 * 32), ("order", ctypes.c_int32 * 32),
                 ("k", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
@@ -65,7 +66,8 @@ class c_stats(ctypes.Structure):
 class c_query_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
                 ("count_only", ctypes.c_int32), ("semantics", ctypes.c_int32),
-                ("order", ctypes.POINTER(ctypes.c_int32)), ("stats", ctypes.POINTER(c_stats))]
+                ("order", ctypes.POINTER(ctypes.c_int32)), ("stats", ctypes.POINTER(c_stats)),
+                ("host_driven", ctypes.c_int32)]
 
 
 class c_query_desc(ctypes.Structure):
@@ -305,7 +307,7 @@ class Graph:
         return out
 
     def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
-              order=None, stats: c_stats | None = None) -> Result:
+              order=None, stats: c_stats | None = None, host_driven: bool = False) -> Result:
         qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
         o = c_query_opts()
         o.stream = _stream_handle(stream)
@@ -313,6 +315,7 @@ class Graph:
         o.mem_budget = mem_budget
         o.count_only = int(count_only)
         o.semantics = 0
+        o.host_driven = int(host_driven)
         ordr = None
         if order is not None:
             ordr = _i32(order)

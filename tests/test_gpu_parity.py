@@ -318,7 +318,7 @@ def test_memory_budget_splits_give_same_result(pkg):
         want = oracle.enumerate_rows(O, q)
         st = pkg.c_stats()
         budget = 1 << 20
-        r = G.query(q, mem_budget=budget, stats=st)
+        r = G.query(q, mem_budget=budget, stats=st, host_driven=True)
         assert r.count == want.shape[0]
         assert np.array_equal(oracle.sort_rows(r.rows()), want)
         assert st.peak_bytes <= budget
@@ -326,11 +326,42 @@ def test_memory_budget_splits_give_same_result(pkg):
     assert split_seen
 
 
+def test_device_driven_overflow_falls_back(pkg):
+    """A budget too small for the device-driven arena's tables: the host-driven path takes over."""
+    g = rmat_graph(34, 12, 40_000, 6, 3)
+    G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
+    O = og(g)
+    sg = synth.make_graph(g.vlab, g.src, g.dst, g.elab, int(g.elab.max()) + 1)
+    for i in range(3):
+        q = synth.walk_query(sg, 6, i, 5, dense=False, max_bound=2e6)
+        want = oracle.enumerate_rows(O, q)
+        for budget in (1 << 18, 1 << 20, 1 << 30):
+            r = G.query(q, mem_budget=budget)
+            assert r.count == want.shape[0]
+            assert np.array_equal(oracle.sort_rows(r.rows()), want)
+
+
+def test_host_and_device_driven_agree(pkg):
+    g = rmat_graph(35, 13, 80_000, 8, 3)
+    G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
+    sg = synth.make_graph(g.vlab, g.src, g.dst, g.elab, int(g.elab.max()) + 1)
+    for i in range(8):
+        q = synth.walk_query(sg, 7, i, int(4 + i % 5), dense=bool(i % 2), max_bound=5e6)
+        a = G.query(q)
+        b = G.query(q, host_driven=True)
+        assert a.count == b.count
+        assert np.array_equal(oracle.sort_rows(a.rows()), oracle.sort_rows(b.rows()))
+        for cap in (1, 17):
+            c = G.query(q, row_cap=cap)
+            assert c.count == a.count and c.rows().shape[0] == min(cap, a.count)
+        assert G.query(q, count_only=True).count == a.count
+
+
 def test_budget_too_small_is_enomem(pkg):
     g = H.complete(30)
     G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
     with pytest.raises(pkg.GsiError) as e:
-        G.query(H.path_query(3), mem_budget=64)
+        G.query(H.path_query(3), mem_budget=64, host_driven=True)
     assert e.value.status == pkg.GSI_ENOMEM
 
 
