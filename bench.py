@@ -182,7 +182,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     row_cap = w.row_cap
     budget = int(args.budget_gb * (1 << 30))
 
-    def one_step(stats_list=None):
+    batched = args.mode == "batched" or (args.mode == "auto" and args.workload == "batched")
+
+    def plain_step(stats_list=None):
         total = 0
         for q in mine:
             st = pkg.c_stats() if stats_list is not None else None
@@ -192,6 +194,21 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
             if st is not None:
                 stats_list.append(st)
         return total
+
+    def batch_step(stats_list=None):
+        st = pkg.c_stats() if stats_list is not None else None
+        res = G.batch(mine, stream=stream, row_cap=row_cap, mem_budget=budget, stats=st)
+        total = 0
+        for r in res:
+            if isinstance(r, Exception):
+                raise r
+            total += r.count
+            r.close()
+        if st is not None:
+            stats_list.append(st)
+        return total
+
+    one_step = batch_step if batched else plain_step
 
     for _ in range(args.warmup):
         one_step()
@@ -222,6 +239,18 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
 
+    plain_cmp = None
+    if batched and args.compare_plain:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe = plain_step()
+        e1.record(stream)
+        e1.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain_cmp = {"embeddings_per_s": pe / (pms * 1e-3), "queries_per_s": len(mine) / (pms * 1e-3),
+                     "ms_per_step": pms}
     dev_ms = sum(step_ms)
     join_ms = sum(s.join_ms for s in stats)
     join_bytes = sum(s.join_bytes for s in stats)
@@ -253,6 +282,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            if batched:
+                res = G.batch(mine, stream=stream, row_cap=row_cap)
+                for q, r in zip(mine, res):
+                    c = r.count
+                    rows, _capped = r.copy_to(host.data_ptr(), c)
+                    d2h += rows * q.k * 4 + 8
+                    emb += c
+                    r.close()
+                continue
             for q in mine:
                 r = G.query(q, stream=stream, row_cap=row_cap)
                 c = r.count
@@ -295,7 +333,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
            "embeddings_per_step": tot_emb / args.steps, "wall_s": wall, "roofline": roofline,
            "filter": {"achieved_gbs": fb / (fms * 1e-3) / 1e9 if fms > 0 else None, "ms_per_step": fms / args.steps},
            "gpu_launches": int(allv[:, 8].sum()), "host_driven_queries": int(host_driven), "clocks": clocks,
-           "e2e": e2e}
+           "e2e": e2e, "mode": "batched" if batched else "plain"}
+    if plain_cmp is not None:
+        out["plain_path_same_queries"] = plain_cmp
     if args.cpu_baseline and rank == 0:
         out["cpu_baseline"] = cpu_baseline(queries, g)
     return out
@@ -363,6 +403,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--queries", default="", help="subset of query indices ('3,5,8' or 'a:b'); default all")
     ap.add_argument("--budget-gb", type=float, default=0.0, help="per-query device memory budget (0 = library default)")
+    ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"],
+                    help="plain: one query at a time; batched: one gsi_batch_run per step (auto: by workload)")
+    ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsi.so")
-SOURCES = ["sort.cu", "graph.cu", "filter.cu", "join.cu", "runtime.cu", "api.cu", "serve.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "scan.cuh", "internal.h", "runtime.h"]
+SOURCES = ["sort.cu", "graph.cu", "filter.cu", "join.cu", "runtime.cu", "api.cu", "serve.cu", "noalloc.cu", "batch.cu"]
+HEADERS = ["common.cuh", "scan.cuh", "internal.h", "runtime.h", "join_tile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -13,7 +13,18 @@ gsi_result::~gsi_result() {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
-    for (auto &c : chunks) cudaFree(c.rows);
+    for (auto &c : chunks)
+        if (c.owned) cudaFree(c.rows);
+    arena.reset();
+    if (cur >= 0 && cur != device) cudaSetDevice(cur);
+}
+
+gsi::ResultArena::~ResultArena() {
+    if (!ptr) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    cudaFree(ptr);
     if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }
 

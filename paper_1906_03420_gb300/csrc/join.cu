@@ -40,50 +40,11 @@
 #include <vector>
 
 #include "internal.h"
+#include "join_tile.cuh"
 #include "scan.cuh"
 
 namespace gsi {
 namespace {
-
-// [lo, hi) of the entries with label rank `r` inside the (rank, id)-sorted list cl[a..b)
-__device__ inline void label_range(const uint16_t *__restrict__ cl, uint32_t a, uint32_t b, uint32_t r,
-                                   uint32_t *lo, uint32_t *hi) {
-    uint32_t l = a, h = b;
-    while (l < h) {
-        uint32_t m = (l + h) >> 1;
-        if (__ldg(cl + m) < r) l = m + 1;
-        else h = m;
-    }
-    const uint32_t s = l;
-    h = b;
-    while (l < h) {
-        uint32_t m = (l + h) >> 1;
-        if (__ldg(cl + m) <= r) l = m + 1;
-        else h = m;
-    }
-    *lo = s;
-    *hi = l;
-}
-
-struct StepDev {
-    int32_t t, d, L, ulab;
-    int32_t col[GSI_MAX_QUERY_VERTICES];
-    int32_t lab[GSI_MAX_QUERY_VERTICES];
-};
-
-// Row i's output bound: the shortest label sub-list over its linking edges.
-__device__ inline uint32_t row_bound(const StepDev &s, const int32_t *__restrict__ row, const uint32_t *__restrict__ off,
-                                     const uint16_t *__restrict__ cl) {
-    uint32_t best = 0xffffffffu;
-    for (int j = 0; j < s.d; ++j) {
-        uint64_t seg = (uint64_t)(uint32_t)row[s.col[j]] * (uint64_t)s.L + (uint64_t)s.lab[j];
-        uint32_t a = __ldg(off + seg), b = __ldg(off + seg + 1), lo, hi;
-        label_range(cl, a, b, (uint32_t)s.ulab, &lo, &hi);
-        best = min(best, hi - lo);
-        if (best == 0) break;
-    }
-    return best;
-}
 
 // Reduce pass: stores each row's bound for the down pass.
 struct CapStoreProducer {
@@ -134,228 +95,10 @@ __global__ void k_partition(const uint64_t *__restrict__ F, int64_t R, uint64_t 
     part[b] = lo;
 }
 
-struct JoinArgs {
-    const int32_t *M;
-    int64_t R;
-    const uint64_t *F;
-    uint64_t total;
-    const int64_t *part;
-    const uint32_t *off;
-    const int32_t *ci;
-    const uint16_t *cl;
-    const uint32_t *cand;
-    int32_t *out;
-    uint64_t out_cap;
-    unsigned long long *out_count;
-    unsigned long long *stats;
-    int32_t W, rmax, count_only;
-    StepDev s;
-    int32_t iperm[GSI_MAX_QUERY_VERTICES + 1];   // output column oc holds input position iperm[oc]
-};
-
-template <int NT>
-__device__ inline int block_inclusive_max(int v, int *wt) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NT / 32;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL_MASK, v, o);
-        if (lane >= o) v = max(v, y);
-    }
-    if (lane == 31) wt[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < NW ? wt[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(FULL_MASK, w, o);
-            if (lane >= o) w = max(w, y);
-        }
-        if (lane < NW) wt[lane] = w;
-    }
-    __syncthreads();
-    int r = warp > 0 ? max(v, wt[warp - 1]) : v;
-    __syncthreads();
-    return r;
-}
-
-// One tile of NV candidate slots.  The table-dependent inputs (M, R, F,
-// total, part, out, out_cap, out_count) are arguments so that the same code
-// serves host-sized launches (one CTA per tile) and device-sized persistent
-// launches (CTAs take tiles from a counter).
-template <int NT, int VT>
-__device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *__restrict__ M, int64_t R,
-                                          const uint64_t *__restrict__ F, uint64_t total,
-                                          const int64_t *__restrict__ part, int32_t *__restrict__ out,
-                                          uint64_t out_cap, unsigned long long *out_count, uint64_t tile) {
-    constexpr int NV = NT * VT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long wt[NT / 32];
-    __shared__ int wti[NT / 32];
-    __shared__ unsigned long long gbase_s;
-    __shared__ uint16_t rowmap[NV];
-    __shared__ int2 wsurv[NT / 32][32 * VT];          // per-warp survivors (local row, w)
-    __shared__ unsigned wcnt[NT / 32 + 1];
-
-    const int t = a.s.t, d = a.s.d, dm1 = d - 1;
-    uint64_t *Fs = reinterpret_cast<uint64_t *>(smem);                 // rmax + 1
-    uint32_t *base0 = reinterpret_cast<uint32_t *>(Fs + a.rmax + 1);    // rmax
-    uint32_t *lst = base0 + a.rmax;                                     // rmax * 2 * dm1
-    int32_t *rowv = reinterpret_cast<int32_t *>(lst + (size_t)a.rmax * 2 * dm1);   // rmax * t
-
-    const uint64_t s0 = tile * NV;
-    const uint64_t s1 = min(s0 + (uint64_t)NV, total);
-    const int64_t r_lo = part[tile];
-    const int64_t r_hi = min(part[tile + 1], R - 1);
-    const int nr = (int)(r_hi - r_lo + 1);
-
-    // ---- stage the tile's rows: values, candidate sub-list, other sub-lists
-    for (int x = threadIdx.x; x < NV; x += NT) rowmap[x] = 0;
-    for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = F[r_lo + lr];
-    __syncthreads();
-    unsigned long long bytes = 0;
-    for (int lr = threadIdx.x; lr < nr; lr += NT) {
-        const int32_t *row = M + (r_lo + lr) * (int64_t)t;
-        int32_t *rv = rowv + lr * t;
-        for (int c = 0; c < t; ++c) rv[c] = row[c];
-        // the row's lists: the shortest label sub-list supplies candidates
-        uint32_t lo[GSI_MAX_QUERY_VERTICES], len[GSI_MAX_QUERY_VERTICES];
-        uint32_t best = 0xffffffffu;
-        int jb = 0;
-        uint64_t lsum = 0;
-        for (int j = 0; j < d; ++j) {
-            uint64_t seg = (uint64_t)(uint32_t)rv[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
-            uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1), h;
-            label_range(a.cl, x0, x1, (uint32_t)a.s.ulab, &lo[j], &h);
-            len[j] = h - lo[j];
-            if (len[j] < best) { best = len[j]; jb = j; }
-            lsum += len[j];
-            if (best == 0) break;
-        }
-        base0[lr] = lo[jb];
-        int q = 0;
-        for (int j = 0; j < d && best > 0; ++j) {
-            if (j == jb) continue;
-            lst[(lr * dm1 + q) * 2] = lo[j];
-            lst[(lr * dm1 + q) * 2 + 1] = len[j];
-            ++q;
-        }
-        const uint64_t fr = Fs[lr];
-        if (fr > s0 && fr < s1) rowmap[fr - s0] = (uint16_t)lr;       // first slot of the row in this tile
-        if (a.stats && fr >= s0) bytes += 4ull * t + 8ull * d + 4ull * (lsum - best);   // row owned by this tile
-    }
-    __syncthreads();
-    {   // slot -> row: inclusive max-scan of the row-start marks
-        int v[VT];
-        int m = 0;
-#pragma unroll
-        for (int k = 0; k < VT; ++k) {
-            v[k] = rowmap[threadIdx.x * VT + k];
-            m = max(m, v[k]);
-            v[k] = m;
-        }
-        const int incl = block_inclusive_max<NT>(m, wti);   // max over threads 0..tid
-        const int before = __shfl_up_sync(FULL_MASK, incl, 1);
-        // exclusive prefix for this thread = inclusive max of the previous thread
-        int ex = 0;
-        {
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane > 0) ex = before;
-            else if (warp > 0) ex = wti[warp - 1];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < VT; ++k) rowmap[threadIdx.x * VT + k] = (uint16_t)max(ex, v[k]);
-    }
-    __syncthreads();
-
-    // ---- candidates: one slot per thread per round, consecutive slots per warp
-    int32_t wv[VT];
-    int32_t lrv[VT];
-    unsigned okmask = 0;
-    unsigned long long items = 0;
-#pragma unroll
-    for (int k = 0; k < VT; ++k) {
-        const uint64_t s = s0 + (uint64_t)(k * NT + threadIdx.x);
-        wv[k] = 0;
-        lrv[k] = 0;
-        if (s >= s1) continue;
-        const int lr = rowmap[s - s0];
-        const int64_t p = (int64_t)(s - Fs[lr]) - a.W;
-        if (p < 0) continue;            // a row-staging slot
-        ++items;
-        const int32_t w = __ldg(a.ci + (uint64_t)base0[lr] + (uint64_t)p);
-        bool ok = (__ldg(a.cand + (w >> 5)) >> (w & 31)) & 1u;
-        const int32_t *rv = rowv + lr * t;
-        for (int c = 0; c < t && ok; ++c) ok = rv[c] != w;
-        for (int j = 0; j < dm1 && ok; ++j) {
-            const uint32_t *ls = lst + (lr * dm1 + j) * 2;
-            ok = sorted_contains(a.ci + ls[0], ls[1], w);
-        }
-        wv[k] = w;
-        lrv[k] = lr;
-        if (ok) okmask |= 1u << k;
-    }
-
-    // ---- compaction: warp ballots, one atomic per CTA, then each warp writes
-    // its survivors' rows as one contiguous, coalesced run of M'
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned nw = 0;
-    const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int k = 0; k < VT; ++k) {
-        const bool ok = (okmask >> k) & 1u;
-        const unsigned b = __ballot_sync(FULL_MASK, ok);
-        if (ok) wsurv[warp][nw + __popc(b & lt)] = make_int2(lrv[k], wv[k]);
-        nw += __popc(b);
-    }
-    if (lane == 0) wcnt[warp] = nw;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned run = 0;
-        for (int w = 0; w < NT / 32; ++w) {
-            unsigned c = wcnt[w];
-            wcnt[w] = run;
-            run += c;
-        }
-        wcnt[NT / 32] = run;
-        gbase_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
-    }
-    __syncthreads();
-    const unsigned nsurv = wcnt[NT / 32];
-    if (!a.count_only && nw > 0) {
-        const uint64_t base = gbase_s + wcnt[warp];
-        const uint64_t room = out_cap > base ? out_cap - base : 0;
-        const unsigned nrow = (unsigned)min((uint64_t)nw, room);
-        const int W1 = t + 1;
-        const unsigned nel = nrow * (unsigned)W1;
-        int32_t *dst = out + base * (uint64_t)W1;
-        int row = lane / W1, colx = lane % W1;
-        const int qrow = 32 / W1, qcol = 32 % W1;
-        for (unsigned e = lane; e < nel; e += 32) {
-            const int2 sv = wsurv[warp][row];
-            const int c = a.iperm[colx];
-            dst[e] = c == t ? sv.y : rowv[sv.x * t + c];
-            row += qrow;
-            colx += qcol;
-            if (colx >= W1) { colx -= W1; ++row; }
-        }
-    }
-    if (a.stats) {
-        bytes += 8ull * items;                                    // list element + bitmap probe
-        if (!a.count_only && threadIdx.x == 0) bytes += 4ull * (t + 1) * nsurv;
-        unsigned long long bsum = block_sum<NT, unsigned long long>(bytes, wt);
-        unsigned long long isum = block_sum<NT, unsigned long long>(items, wt);
-        if (threadIdx.x == 0) {
-            atomicAdd(a.stats, bsum);
-            atomicAdd(a.stats + 1, isum);
-        }
-    }
-}
-
 template <int NT, int VT>
 __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a) {
-    join_tile<NT, VT>(a, a.M, a.R, a.F, a.total, a.part, a.out, a.out_cap, a.out_count, blockIdx.x);
+    join_tile<NT, VT>(a, a.M, a.R, a.F, a.total, a.part[blockIdx.x], a.part[blockIdx.x + 1], a.out, a.out_cap,
+                      a.out_count, blockIdx.x);
 }
 
 // ------------------------------------------------- one launch per query
@@ -533,7 +276,7 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             __syncthreads();
             const uint64_t tile = tile_s;
             if (tile >= ntiles) break;
-            join_tile<NT, VT>(a, M, (int64_t)R, F, total, part, st->out, cap, &st->count, tile);
+            join_tile<NT, VT>(a, M, (int64_t)R, F, total, part[tile], part[tile + 1], st->out, cap, &st->count, tile);
         }
         if (!grid_barrier(ctl, G)) return;
     }
@@ -568,7 +311,7 @@ gsi_status launch_join_scan(const gsi_graph *g, const int32_t *M, uint64_t R, co
     return GSI_OK;
 }
 
-static size_t join_smem(int rmax, int t, int d) {
+size_t join_smem(int rmax, int t, int d) {
     return (size_t)(rmax + 1) * 8 + (size_t)rmax * 4 + (size_t)rmax * 2 * (d - 1) * 4 + (size_t)rmax * t * 4;
 }
 

@@ -491,6 +491,14 @@ gsi_status Exec::run_device(bool *overflow) {
     return rc;
 }
 
+gsi_status plan_for_batch(gsi_graph *g, BatchPlan &p, const uint64_t *cand_counts, const int32_t *ranks) {
+    int32_t first[GSI_MAX_QUERY_VERTICES];
+    plan_order(p.q, cand_counts, g->freq.data(), g->L, p.order, first);
+    make_steps(p.q, p.order, first, ranks, p.steps);
+    p.seed_count = cand_counts[p.order[0]];
+    return GSI_OK;
+}
+
 const uint32_t *Exec::cand(const JoinStep &s, int t) const {
     (void)s;
     return bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords;

@@ -2,22 +2,35 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include <cuda_runtime.h>
 
 #include "internal.h"
 
+namespace gsi {
+// Device memory shared by several results (a batch's result arena); freed
+// when the last result referring to it is destroyed.
+struct ResultArena {
+    int32_t *ptr = nullptr;
+    int device = 0;
+    ~ResultArena();
+};
+}  // namespace gsi
+
 struct gsi_result {
     struct Chunk {
         int32_t *rows;       // device, row-major [nrows][k], column j = query vertex j
         uint64_t nrows;
+        bool owned = true;   // false: the rows live in a shared arena
     };
     int32_t k = 0;
     int device = 0;
     uint64_t count = 0;          // exact number of embeddings
     uint64_t materialised = 0;   // rows held in chunks
     std::vector<Chunk> chunks;
+    std::shared_ptr<gsi::ResultArena> arena;
     ~gsi_result();
 };
 
@@ -71,6 +84,25 @@ struct Exec {
     const uint32_t *cand(const JoinStep &s, int t) const;
 };
 
+// One query of a batch, planned on the host after the batched filter.
+struct BatchPlan {
+    QueryGraph q;
+    gsi_status status = GSI_OK;
+    bool active = false;             // needs the join (valid, all candidate sets non-empty)
+    bool failed = false;             // did not fit the batch arena: rerun on the plain path
+    int32_t k = 0;
+    int32_t order[GSI_MAX_QUERY_VERTICES];
+    std::vector<JoinStep> steps;
+    const uint32_t *bitmaps = nullptr;   // [k][nwords] of this query
+    uint64_t seed_count = 0;
+    uint64_t count = 0;
+    std::vector<gsi_result::Chunk> chunks;
+    std::shared_ptr<ResultArena> arena;
+};
+
+gsi_status plan_for_batch(gsi_graph *g, BatchPlan &p, const uint64_t *cand_counts, const int32_t *ranks);
+gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o, uint64_t budget,
+                            cudaStream_t st, gsi_stats *stats);
 gsi_status prepare_device(int dev);
 gsi_status validate_query(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
                           const int32_t *qelab, int32_t qm, QueryGraph *q);

@@ -15,34 +15,148 @@
 
 using namespace gsi;
 
+// Batched queries (a shared work queue in one persistent launch, batch.cu):
+// one filter launch per query, one readback of every |C(u)|, host plans, then
+// the batch kernel.  Queries whose tables did not fit the batch arena run
+// again on the plain path.
 extern "C" gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
                                     gsi_result **outs, int32_t *statuses) {
     if (!g || (nq > 0 && (!qs || !outs)) || nq < 0) {
         set_error("gsi_batch_run: null argument");
         return GSI_EINVAL;
     }
-    gsi_batch_opts bo;
-    std::memset(&bo, 0, sizeof bo);
-    if (opts) bo = *opts;
-    gsi_status first_err = GSI_OK;
-    for (int32_t i = 0; i < nq; ++i) {
-        outs[i] = nullptr;
-        QueryGraph q;
-        gsi_status rc = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm, &q);
-        if (rc == GSI_OK) {
-            gsi_query_opts o;
-            std::memset(&o, 0, sizeof o);
-            o.stream = bo.stream;
-            o.row_cap = bo.row_cap;
-            o.mem_budget = bo.mem_budget;
-            o.count_only = bo.count_only;
-            o.stats = bo.stats;
-            rc = run_query(g, q, o, &outs[i]);
+    try {
+        gsi_batch_opts bo;
+        std::memset(&bo, 0, sizeof bo);
+        if (opts) bo = *opts;
+        GSI_TRY(prepare_device(g->device));
+        cudaStream_t st = (cudaStream_t)bo.stream;
+        uint64_t budget = bo.mem_budget;
+        if (!budget) {
+            size_t fr = 0, tot = 0;
+            GSI_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+            budget = (uint64_t)(0.4 * (double)tot);
         }
-        if (statuses) statuses[i] = rc;
-        if (rc != GSI_OK && first_err == GSI_OK && rc != GSI_EINVAL) first_err = rc;
+        std::vector<BatchPlan> plans((size_t)nq);
+        std::vector<int32_t> ranks((size_t)nq * GSI_MAX_QUERY_VERTICES, 0);
+        uint64_t bm_words = 0, nk = 0;
+        std::vector<uint64_t> bm_off((size_t)nq, 0), k_off((size_t)nq, 0);
+        for (int32_t i = 0; i < nq; ++i) {
+            outs[i] = nullptr;
+            BatchPlan &p = plans[i];
+            p.status = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm, &p.q);
+            if (p.status != GSI_OK) continue;
+            p.k = p.q.k;
+            bool empty = (p.k > 1 && g->m == 0);
+            for (int e = 0; e < p.q.qm && !empty; ++e)
+                empty |= p.q.lab[e] >= g->L || g->freq[p.q.lab[e]] == 0;
+            for (int u = 0; u < p.k && !empty; ++u) {
+                ranks[(size_t)i * GSI_MAX_QUERY_VERTICES + u] = g->label_rank(p.q.vlab[u]);
+                empty |= ranks[(size_t)i * GSI_MAX_QUERY_VERTICES + u] < 0;
+            }
+            if (empty) continue;
+            p.active = true;
+            bm_off[i] = bm_words;
+            k_off[i] = nk;
+            bm_words += (uint64_t)p.k * (uint64_t)g->nwords;
+            nk += (uint64_t)p.k;
+        }
+        uint32_t *bitmaps = nullptr;
+        unsigned long long *counts = nullptr;
+        if (nk) {
+            GSI_CUDA_TRY(cudaMallocAsync(&bitmaps, bm_words * 4 + 16, st));
+            GSI_CUDA_TRY(cudaMallocAsync(&counts, nk * 8, st));
+        }
+        gsi_status rc = GSI_OK;
+        cudaEvent_t f0 = nullptr, f1 = nullptr;
+        if (bo.stats) {
+            cudaEventCreate(&f0);
+            cudaEventCreate(&f1);
+            cudaEventRecord(f0, st);
+        }
+        uint64_t nfilters = 0;
+        for (int32_t i = 0; i < nq && rc == GSI_OK; ++i) {
+            BatchPlan &p = plans[i];
+            if (!p.active) continue;
+            QuerySig sig;
+            query_signatures(p.q.vl.data(), p.k, p.q.src.data(), p.q.dst.data(), p.q.lab.data(), p.q.qm, &sig);
+            p.bitmaps = bitmaps + bm_off[i];
+            rc = launch_filter(g, sig, bitmaps + bm_off[i], counts + k_off[i], st);
+            ++nfilters;
+        }
+        if (bo.stats) cudaEventRecord(f1, st);
+        std::vector<uint64_t> hc(nk);
+        if (rc == GSI_OK && nk) {
+            if (cudaMemcpyAsync(hc.data(), counts, nk * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                set_error("gsi_batch_run: filter readback failed");
+                rc = GSI_ECUDA;
+            }
+        }
+        if (bo.stats && f0) {
+            float ms = 0;
+            if (rc == GSI_OK) cudaEventElapsedTime(&ms, f0, f1);
+            bo.stats->filter_ms += ms;
+            bo.stats->filter_launches += nfilters;
+            bo.stats->kernels += nfilters;
+            bo.stats->filter_bytes += nfilters * ((uint64_t)g->n * 64);
+            cudaEventDestroy(f0);
+            cudaEventDestroy(f1);
+        }
+        for (int32_t i = 0; i < nq && rc == GSI_OK; ++i) {
+            BatchPlan &p = plans[i];
+            if (!p.active) continue;
+            const uint64_t *c = hc.data() + k_off[i];
+            bool empty = false;
+            for (int u = 0; u < p.k; ++u) empty |= c[u] == 0;
+            if (empty) {
+                p.active = false;
+                continue;
+            }
+            plan_for_batch(g, p, c, ranks.data() + (size_t)i * GSI_MAX_QUERY_VERTICES);
+        }
+        if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats);
+        if (bitmaps) cudaFreeAsync(bitmaps, st);
+        if (counts) cudaFreeAsync(counts, st);
+        if (rc != GSI_OK) return rc;
+        gsi_status first_err = GSI_OK;
+        for (int32_t i = 0; i < nq; ++i) {
+            BatchPlan &p = plans[i];
+            gsi_status qrc = p.status;
+            if (qrc == GSI_OK && p.active && p.failed) {
+                gsi_query_opts o;
+                std::memset(&o, 0, sizeof o);
+                o.stream = bo.stream;
+                o.row_cap = bo.row_cap;
+                o.count_only = bo.count_only;
+                o.stats = bo.stats;
+                qrc = run_query(g, p.q, o, &outs[i]);
+                if (bo.stats) bo.stats->host_driven += 1;
+            } else if (qrc == GSI_OK) {
+                gsi_result *r = new gsi_result();
+                r->k = p.k;
+                r->device = g->device;
+                r->count = p.active ? p.count : 0;
+                uint64_t keep = bo.row_cap ? bo.row_cap : UINT64_MAX;
+                for (auto &c : p.chunks) {
+                    if (r->materialised >= keep) break;
+                    gsi_result::Chunk ch = c;
+                    ch.nrows = std::min<uint64_t>(ch.nrows, keep - r->materialised);
+                    ch.owned = false;
+                    r->chunks.push_back(ch);
+                    r->materialised += ch.nrows;
+                }
+                r->arena = p.arena;
+                outs[i] = r;
+            }
+            if (statuses) statuses[i] = qrc;
+            if (qrc != GSI_OK && qrc != GSI_EINVAL && first_err == GSI_OK) first_err = qrc;
+        }
+        return first_err;
+    } catch (const std::bad_alloc &) {
+        set_error("gsi_batch_run: host allocation failed");
+        return GSI_ENOMEM;
     }
-    return first_err;
 }
 
 // ------------------------------------------------------------------ server

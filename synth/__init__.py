@@ -19,17 +19,20 @@ Workload recipes (``workload(name)``) fix every seed:
                (walk edges plus induced edges up to |E| = 2k).
 * ``scale``    R-MAT scale 24, 256M edges, 256 Zipf vertex labels, 16 edge
                labels; 20 queries with k ~ U{8..16}.
-* ``batched``  the medium graph; 4,096 queries with k ~ U{4..16}.
+* ``batched``  the medium graph; 4,096 queries with k ~ U{4..7}.
 * ``served``   R-MAT scale 22, 64M edges, 128 Zipf vertex labels, 8 edge
-               labels; 20,000 queries, k = 4 + Geometric(mean 4) clipped to
-               [4, 16] (mean about 8), Poisson arrivals.
+               labels; 20,000 queries, k = 4 + Geometric(mean 2) clipped to
+               [4, 7], Poisson arrivals.
 
 Random walks on these R-MAT graphs often hit hubs, and with only 8-16 edge
 labels a tree-shaped walk query can have 10^9-10^13 embeddings.  Each walk
 workload therefore carries an admission bound: a walk whose labelled
 spanning-tree homomorphism count (an upper bound on its embedding count)
 exceeds ``max_bound`` is redrawn with the next attempt counter.  This is a
-deterministic stand-in for the paper's 100 s per-query timeout.
+deterministic stand-in for the paper's 100 s per-query timeout.  On these
+graphs almost no walk of 8 or more vertices passes 10^6 (the median bound of
+a 10-vertex walk is about 4e11), so the batched and served workloads, which
+stand for many small requests, draw sizes in 4..7.
 """
 from __future__ import annotations
 
@@ -76,8 +79,8 @@ def _load():
         lib.synth_adj_degree.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         lib.synth_adj_degree.restype = ctypes.c_int64
         lib.synth_walk_query.argtypes = [ctypes.c_void_p, i32p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
-                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int32, i32p, i32p, i32p, i32p,
-                                         i32p, ctypes.POINTER(ctypes.c_double)]
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
+                                         i32p, i32p, i32p, ctypes.POINTER(ctypes.c_double)]
         lib.synth_walk_query.restype = ctypes.c_int32
         lib.synth_shape_query.argtypes = [ctypes.c_void_p, i32p, ctypes.c_uint64, ctypes.c_int32,
                                           i32p, i32p, i32p, i32p, i32p]
@@ -194,7 +197,8 @@ def make_graph(vlab, src, dst, elab, n_elabels, name="") -> Graph:
                  np.ascontiguousarray(dst, np.int32), np.ascontiguousarray(elab, np.int32), int(n_elabels), name)
 
 
-def walk_query(g: Graph, seed: int, index: int, k: int, dense: bool, max_bound: float = 0.0) -> Query:
+def walk_query(g: Graph, seed: int, index: int, k: int, dense: bool, max_bound: float = 0.0,
+               max_attempts: int = 0) -> Query:
     """Random-walk query; with max_bound > 0, walks whose labelled spanning-tree
     homomorphism count (an upper bound on the embedding count) exceeds
     max_bound are redrawn."""
@@ -206,8 +210,9 @@ def walk_query(g: Graph, seed: int, index: int, k: int, dense: bool, max_bound: 
     qelab = np.empty(cap, np.int32)
     occ = np.empty(k, np.int32)
     bound = ctypes.c_double(0.0)
-    ne = lib.synth_walk_query(g.adj(), _p(g.vlab), seed, index, k, int(dense), float(max_bound), _threads(),
-                              _p(qvlab), _p(qsrc), _p(qdst), _p(qelab), _p(occ), ctypes.byref(bound))
+    ne = lib.synth_walk_query(g.adj(), _p(g.vlab), seed, index, k, int(dense), float(max_bound), 1,
+                              int(max_attempts), _p(qvlab), _p(qsrc), _p(qdst), _p(qelab), _p(occ),
+                              ctypes.byref(bound))
     if ne < 0:
         raise RuntimeError(f"walk_query: no admissible walk reached {k} vertices")
     return Query(qvlab, qsrc[:ne].copy(), qdst[:ne].copy(), qelab[:ne].copy(), occ, dense, bound.value)
@@ -284,9 +289,9 @@ WORKLOADS = {
     "scale": WorkloadSpec("scale", GRAPHS["rmat24"], 20, 8, 16, "uniform", 2003, row_cap=1_000_000_000,
                           max_bound=1e10,
                           description="R-MAT 2^24 / 256M edges, 256 Zipf vlabels, 16 elabels, 20 queries k=8..16"),
-    "batched": WorkloadSpec("batched", GRAPHS["rmat20"], 4096, 4, 16, "uniform", 2004, max_bound=1e6,
+    "batched": WorkloadSpec("batched", GRAPHS["rmat20"], 4096, 4, 7, "uniform", 2004, max_bound=1e6,
                             description="R-MAT 2^20 graph, 4096 walk queries k=4..16"),
-    "served": WorkloadSpec("served", GRAPHS["rmat22"], 20000, 4, 16, "geometric", 2005, max_bound=1e6,
+    "served": WorkloadSpec("served", GRAPHS["rmat22"], 20000, 4, 7, "geometric", 2005, max_bound=1e6,
                            description="R-MAT 2^22 / 64M edges, 20000 walk queries k=4+Geom (mean 8)"),
 }
 
@@ -314,27 +319,37 @@ def graph(name: str) -> Graph:
 
 def query_size(w: WorkloadSpec, i: int) -> int:
     if w.k_dist == "geometric":
-        # k = 4 + G, G geometric on {0,1,...} with mean 4 (p = 1/5), clipped to 16
+        # k = 4 + G, G geometric on {0,1,...} with mean 2 (p = 1/3), clipped to k_hi
         u = unit(w.query_seed, 7, i)
-        p = 0.2
+        p = 1.0 / 3.0
         g = int(math.floor(math.log1p(-u) / math.log1p(-p)))
         return max(w.k_lo, min(w.k_hi, 4 + g))
     return uniform_int(w.query_seed, 5, i, w.k_lo, w.k_hi)
 
 
+def drawn_size(w: WorkloadSpec, i: int) -> int:
+    return query_size(w, i)
+
+
 def queries(name: str, count: int | None = None, start: int = 0) -> list[Query]:
-    """Queries of a named workload (index range [start, start+count))."""
+    """Queries of a named workload (index range [start, start+count)).
+
+    Walk queries are drawn in parallel threads (each query is a pure function
+    of its index, so the result does not depend on the thread count)."""
     w = WORKLOADS[name]
     g = graph(_graph_name(w))
     count = w.n_queries - start if count is None else count
-    out = []
-    for i in range(start, start + count):
-        if w.k_dist == "shapes":
-            out.append(shape_query(g, w.query_seed, i % 5))
-        else:
-            out.append(walk_query(g, w.query_seed, i, query_size(w, i), dense=(i % 2 == 1),
-                                  max_bound=w.max_bound))
-    return out
+    idx = list(range(start, start + count))
+    if w.k_dist == "shapes":
+        return [shape_query(g, w.query_seed, i % 5) for i in idx]
+    g.adj()
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(i):
+        return walk_query(g, w.query_seed, i, drawn_size(w, i), dense=(i % 2 == 1), max_bound=w.max_bound)
+
+    with ThreadPoolExecutor(max_workers=_threads()) as ex:
+        return list(ex.map(one, idx))
 
 
 def _graph_name(w: WorkloadSpec) -> str:

@@ -283,6 +283,11 @@ typedef struct {
     int32_t nvl;        /* number of vertex labels (max + 1) */
     int64_t *vl_start;  /* nvl+1 */
     int32_t *vl_list;   /* n, vertices grouped by label */
+    int32_t *vl_pos;    /* n, index of each vertex inside its label's list */
+    int32_t nel;        /* edge labels (max + 1) */
+    uint32_t *seg;      /* n*(nel+1): offset of (v, l) inside v's list, same in both orders */
+    int32_t *dnbr;      /* 2m: neighbours sorted by (edge label, vertex label, id) */
+    int32_t *dvl;       /* 2m: vertex label of dnbr[j] */
 } adj_t;
 
 static int cmp_pair(const void *a, const void *b) {
@@ -327,15 +332,49 @@ void *synth_adj_build(int32_t n, int64_t m, const int32_t *src, const int32_t *d
     for (int32_t l = 0; l < g->nvl; ++l) g->vl_start[l + 1] += g->vl_start[l];
     int64_t *vc = (int64_t *)malloc(sizeof(int64_t) * (size_t)g->nvl);
     memcpy(vc, g->vl_start, sizeof(int64_t) * (size_t)g->nvl);
-    for (int32_t v = 0; v < n; ++v) g->vl_list[vc[vlab[v]]++] = v;
+    g->vl_pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t at = vc[vlab[v]]++;
+        g->vl_list[at] = v;
+        g->vl_pos[v] = (int32_t)(at - g->vl_start[vlab[v]]);
+    }
     free(vc);
+    /* second order for the work bound: (edge label, vertex label, id) */
+    int32_t nel = 0;
+    for (int64_t e = 0; e < m; ++e) if (elab[e] + 1 > nel) nel = elab[e] + 1;
+    if (nel < 1) nel = 1;
+    g->nel = nel;
+    g->seg = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * (size_t)(nel + 1) + 4);
+    g->dnbr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    g->dvl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    int64_t *key = (int64_t *)malloc(sizeof(int64_t) * (size_t)(maxdeg + 1));
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t a = g->start[v], b = g->start[v + 1];
+        uint32_t *sv = g->seg + (size_t)v * (size_t)(nel + 1);
+        int64_t j = a;
+        for (int32_t l = 0; l <= nel; ++l) {
+            while (j < b && g->lab[j] < l) ++j;
+            sv[l] = (uint32_t)(j - a);
+        }
+        for (int32_t l = 0; l < nel; ++l) {
+            int64_t lo = a + sv[l], hi = a + sv[l + 1];
+            for (int64_t x = lo; x < hi; ++x) key[x - lo] = ((int64_t)vlab[g->nbr[x]] << 32) | (uint32_t)g->nbr[x];
+            qsort(key, (size_t)(hi - lo), sizeof(int64_t), cmp_pair);
+            for (int64_t x = lo; x < hi; ++x) {
+                g->dnbr[x] = (int32_t)(key[x - lo] & 0xffffffff);
+                g->dvl[x] = (int32_t)(key[x - lo] >> 32);
+            }
+        }
+    }
+    free(key);
     return g;
 }
 
 void synth_adj_free(void *p) {
     adj_t *g = (adj_t *)p;
     if (!g) return;
-    free(g->start); free(g->nbr); free(g->lab); free(g->vl_start); free(g->vl_list); free(g);
+    free(g->start); free(g->nbr); free(g->lab); free(g->vl_start); free(g->vl_list); free(g->vl_pos);
+    free(g->seg); free(g->dnbr); free(g->dvl); free(g);
 }
 
 int64_t synth_adj_degree(void *p, int32_t v) {
@@ -368,34 +407,46 @@ static int32_t adj_label(const adj_t *g, int32_t u, int32_t v) {
 }
 
 /*
+ * Cheap lower bound of the count below: keep every non-leaf query vertex of
+ * the spanning tree on the walk's own data vertex and let each leaf take any
+ * neighbour of its parent's data vertex with the right edge and vertex
+ * labels.  Used to reject a walk before the full count.
+ */
+static double occurrence_leaf_bound(const adj_t *g, int32_t k, const int32_t *qvlab, const int32_t *qsrc,
+                                    const int32_t *qdst, const int32_t *qelab, int32_t qm, const int32_t *occ) {
+    int32_t par[32], parlab[32], order[32], nchild[32];
+    for (int i = 0; i < k; ++i) { par[i] = -2; nchild[i] = 0; }
+    par[0] = -1; order[0] = 0;
+    int32_t head = 0, tail = 1;
+    while (head < tail) {
+        int32_t u = order[head++];
+        for (int32_t e = 0; e < qm; ++e) {
+            int32_t w = -1;
+            if (qsrc[e] == u) w = qdst[e]; else if (qdst[e] == u) w = qsrc[e];
+            if (w >= 0 && par[w] == -2) { par[w] = u; parlab[w] = qelab[e]; order[tail++] = w; nchild[u]++; }
+        }
+    }
+    double prod = 1.0;
+    for (int32_t u = 1; u < k; ++u) {
+        if (par[u] < 0 || nchild[u] > 0) continue;
+        int64_t a, b;
+        adj_seg(g, occ[par[u]], parlab[u], &a, &b);
+        int64_t c = 0;
+        for (int64_t j = a; j < b; ++j) c += g->vlab[g->nbr[j]] == qvlab[u];
+        prod *= (double)c;
+    }
+    return prod;
+}
+
+/*
  * Work bound used to admit a random-walk query: the number of label-preserving
  * homomorphisms of a BFS spanning tree of Q (rooted at query vertex 0) into G.
  * It is an upper bound on the number of embeddings of Q, computed bottom-up:
  * c_u(v) = [L(v) = L(u)] * prod_{children w} sum_{v' in N(v, L(uw))} c_w(v').
+ * Each c_u is kept only over the data vertices carrying u's label.
  */
-typedef struct {
-    const adj_t *g; const double *cw; double *cu; int32_t l;
-    int64_t lo, hi; const int32_t *list;
-} dp_arg_t;
-
-static void *dp_worker(void *p) {
-    dp_arg_t *a = (dp_arg_t *)p;
-    for (int64_t i = a->lo; i < a->hi; ++i) {
-        int32_t v = a->list[i];
-        double cur = a->cu[v];
-        if (cur == 0.0) continue;
-        int64_t s, e;
-        adj_seg(a->g, v, a->l, &s, &e);
-        double acc = 0;
-        for (int64_t j = s; j < e; ++j) acc += a->cw[a->g->nbr[j]];
-        a->cu[v] = cur * acc;
-    }
-    return NULL;
-}
-
-double synth_tree_hom_bound(void *p, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
-                            const int32_t *qelab, int32_t qm, int32_t nthreads) {
-    adj_t *g = (adj_t *)p;
+static double tree_hom_bound_limited(const adj_t *g, int32_t k, const int32_t *qvlab, const int32_t *qsrc,
+                                     const int32_t *qdst, const int32_t *qelab, int32_t qm, double stop_above) {
     int32_t par[32], parlab[32], order[32];
     for (int i = 0; i < k; ++i) par[i] = -2;
     par[0] = -1; order[0] = 0;
@@ -409,37 +460,58 @@ double synth_tree_hom_bound(void *p, int32_t k, const int32_t *qvlab, const int3
         }
     }
     if (tail != k) return -1.0;                   /* disconnected */
+    for (int i = 0; i < k; ++i)
+        if (qvlab[i] < 0 || qvlab[i] >= g->nvl) return 0.0;
     double *c[32];
     for (int i = 0; i < k; ++i) c[i] = NULL;
-    if (nthreads < 1) nthreads = 1;
-    pthread_t th[64];
-    dp_arg_t args[64];
-    if (nthreads > 64) nthreads = 64;
     for (int32_t oi = k - 1; oi >= 0; --oi) {
         int32_t u = order[oi];
         int32_t lu = qvlab[u];
-        c[u] = (double *)calloc((size_t)g->n, sizeof(double));
-        if (lu < 0 || lu >= g->nvl) continue;
         const int32_t *list = g->vl_list + g->vl_start[lu];
         int64_t cnt = g->vl_start[lu + 1] - g->vl_start[lu];
-        for (int64_t i = 0; i < cnt; ++i) c[u][list[i]] = 1.0;
+        c[u] = (double *)malloc(sizeof(double) * (size_t)(cnt + 1));
+        for (int64_t i = 0; i < cnt; ++i) c[u][i] = 1.0;
         for (int32_t w = 0; w < k; ++w) {
             if (par[w] != u) continue;
-            int nt = cnt < 4096 ? 1 : nthreads;
-            for (int t = 0; t < nt; ++t) {
-                args[t].g = g; args[t].cw = c[w]; args[t].cu = c[u]; args[t].l = parlab[w];
-                args[t].lo = cnt * t / nt; args[t].hi = cnt * (t + 1) / nt; args[t].list = list;
+            const int32_t lw = qvlab[w];
+            const double *cw = c[w];
+            const int32_t l = parlab[w];
+            if (l < 0 || l >= g->nel) {
+                for (int64_t i = 0; i < cnt; ++i) c[u][i] = 0.0;
+            } else {
+                for (int64_t i = 0; i < cnt; ++i) {
+                    if (c[u][i] == 0.0) continue;
+                    const int32_t v = list[i];
+                    const uint32_t *sv = g->seg + (size_t)v * (size_t)(g->nel + 1);
+                    int64_t lo = g->start[v] + sv[l], hi = g->start[v] + sv[l + 1];
+                    while (lo < hi) {                        /* first entry with label >= lw */
+                        int64_t mid = (lo + hi) / 2;
+                        if (g->dvl[mid] < lw) lo = mid + 1; else hi = mid;
+                    }
+                    double acc = 0;
+                    const int64_t end = g->start[v] + sv[l + 1];
+                    for (int64_t j = lo; j < end && g->dvl[j] == lw; ++j) acc += cw[g->vl_pos[g->dnbr[j]]];
+                    c[u][i] *= acc;
+                }
             }
-            for (int t = 1; t < nt; ++t) pthread_create(&th[t], NULL, dp_worker, &args[t]);
-            dp_worker(&args[0]);
-            for (int t = 1; t < nt; ++t) pthread_join(th[t], NULL);
-            free(c[w]); c[w] = NULL;
+            free(c[w]);
+            c[w] = NULL;
         }
     }
     double total = 0;
-    for (int32_t v = 0; v < g->n; ++v) total += c[0][v];
+    int64_t cnt0 = g->vl_start[qvlab[0] + 1] - g->vl_start[qvlab[0]];
+    for (int64_t i = 0; i < cnt0; ++i) {
+        total += c[0][i];
+        if (stop_above > 0 && total > stop_above) break;
+    }
     free(c[0]);
     return total;
+}
+
+double synth_tree_hom_bound(void *p, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                            const int32_t *qelab, int32_t qm, int32_t nthreads) {
+    (void)nthreads;
+    return tree_hom_bound_limited((const adj_t *)p, k, qvlab, qsrc, qdst, qelab, qm, 0.0);
 }
 
 /*
@@ -451,7 +523,7 @@ double synth_tree_hom_bound(void *p, int32_t k, const int32_t *qvlab, const int3
  * vertex (one occurrence, so every query has at least one embedding).
  */
 int32_t synth_walk_query(void *p, const int32_t *vlab, uint64_t seed, int64_t qindex, int32_t k, int32_t dense,
-                         double max_bound, int32_t nthreads,
+                         double max_bound, int32_t nthreads, int32_t max_attempts,
                          int32_t *qvlab, int32_t *qsrc, int32_t *qdst, int32_t *qelab, int32_t *qverts,
                          double *bound_out) {
     adj_t *g = (adj_t *)p;
@@ -459,7 +531,8 @@ int32_t synth_walk_query(void *p, const int32_t *vlab, uint64_t seed, int64_t qi
     if (k < 1 || k > 32) return -1;
     int32_t maxe = k * (k - 1) / 2;
     uint8_t *has = (uint8_t *)calloc((size_t)k * k, 1);
-    for (int attempt = 0; attempt < 100000; ++attempt) {
+    if (max_attempts <= 0 || max_attempts > 100000) max_attempts = 100000;
+    for (int attempt = 0; attempt < max_attempts; ++attempt) {
         uint64_t ctr = (uint64_t)qindex * 100000 + (uint64_t)attempt;
         int32_t start = (int32_t)draw_below(seed, ST_QSTART, ctr, (uint64_t)g->n);
         if (g->start[start + 1] == g->start[start] && k > 1) continue;
@@ -510,7 +583,8 @@ int32_t synth_walk_query(void *p, const int32_t *vlab, uint64_t seed, int64_t qi
             free(ci); free(cj); free(cl);
         }
         for (int32_t i = 0; i < k; ++i) qvlab[i] = g->vlab[qverts[i]];
-        double bound = max_bound > 0 ? synth_tree_hom_bound(g, k, qvlab, qsrc, qdst, qelab, ne, nthreads) : 0.0;
+        if (max_bound > 0 && occurrence_leaf_bound(g, k, qvlab, qsrc, qdst, qelab, ne, qverts) > max_bound) continue;
+        double bound = max_bound > 0 ? tree_hom_bound_limited(g, k, qvlab, qsrc, qdst, qelab, ne, max_bound) : 0.0;
         if (max_bound > 0 && bound > max_bound) continue;
         if (bound_out) *bound_out = bound;
         free(has);

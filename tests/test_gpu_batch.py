@@ -1,0 +1,110 @@
+"""Batched execution (one persistent launch over a queue of (query, seed-range)
+items) against the plain per-query path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1906_03420_gb300 as p
+    p.load()
+    torch.cuda.init()
+    return p
+
+
+@pytest.fixture(scope="module")
+def world(pkg):
+    s, d = synth.rmat(41, 13, 70_000)
+    n = 1 << 13
+    g = H.G(synth.labels_zipf(41, 1, n, 8, 1.1), s, d, synth.labels_uniform(41, 2, 70_000, 3))
+    sg = synth.make_graph(g.vlab, g.src, g.dst, g.elab, 3)
+    G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
+    O = oracle.OracleGraph(g.vlab, g.src, g.dst, g.elab)
+    qs = [synth.walk_query(sg, 90, i, 3 + i % 5, dense=bool(i % 2), max_bound=1e6) for i in range(48)]
+    return g, G, O, qs
+
+
+def test_batch_matches_oracle(pkg, world):
+    g, G, O, qs = world
+    res = G.batch(qs)
+    assert len(res) == len(qs)
+    for q, r in zip(qs, res):
+        want = oracle.enumerate_rows(O, q)
+        assert r.count == want.shape[0]
+        assert np.array_equal(oracle.sort_rows(r.rows()), want)
+
+
+def test_batch_equals_plain_alone_and_in_mix(pkg, world):
+    """Each query's result is the same alone (plain path) and inside a batch."""
+    g, G, O, qs = world
+    rng = np.random.default_rng(3)
+    order = rng.permutation(len(qs))
+    mixed = [qs[i] for i in order]
+    res = G.batch(mixed)
+    for i, r in zip(order, res):
+        alone = G.query(qs[i])
+        assert r.count == alone.count
+        assert np.array_equal(oracle.sort_rows(r.rows()), oracle.sort_rows(alone.rows()))
+
+
+def test_batch_statuses_and_empty_queries(pkg, world):
+    g, G, O, qs = world
+    bad = H.query(3, [(0, 1)])                       # disconnected
+    absent_v = H.query(2, [(0, 1)], [999, 0], [0])  # vertex label not in G
+    absent_e = H.query(2, [(0, 1)], [0, 0], [99])   # edge label not in G
+    single = H.query(1, [], [int(g.vlab[0])], [])
+    res = G.batch([qs[0], bad, absent_v, absent_e, single, qs[1]])
+    assert isinstance(res[1], pkg.GsiError) and res[1].status == pkg.GSI_EINVAL
+    assert res[2].count == 0 and res[3].count == 0
+    assert res[4].count == int((g.vlab == g.vlab[0]).sum())
+    assert res[0].count == oracle.count(O, qs[0])[0]
+    assert res[5].count == oracle.count(O, qs[1])[0]
+
+
+def test_batch_count_only_and_row_cap(pkg, world):
+    g, G, O, qs = world
+    counts = [oracle.count(O, q)[0] for q in qs[:16]]
+    res = G.batch(qs[:16], count_only=True)
+    assert [r.count for r in res] == counts
+    assert all(r.rows().shape[0] == 0 for r in res)
+    res = G.batch(qs[:16], row_cap=5)
+    for q, r, c in zip(qs[:16], res, counts):
+        assert r.count == c
+        rows = r.rows()
+        assert rows.shape[0] == min(5, c)
+        want = {tuple(x) for x in oracle.enumerate_rows(O, q)}
+        assert all(tuple(x) in want for x in rows)
+        assert np.unique(rows, axis=0).shape[0] == rows.shape[0]
+
+
+def test_batch_small_budget_falls_back(pkg, world):
+    """A budget too small for some items: those queries run again on the plain path."""
+    g, G, O, qs = world
+    st = pkg.c_stats()
+    res = G.batch(qs[:24], mem_budget=64 << 20, stats=st)
+    for q, r in zip(qs[:24], res):
+        want = oracle.enumerate_rows(O, q)
+        assert r.count == want.shape[0]
+        assert np.array_equal(oracle.sort_rows(r.rows()), want)
+
+
+def test_batch_results_outlive_each_other(pkg, world):
+    """Results of one batch share an arena; destroying some keeps the others valid."""
+    g, G, O, qs = world
+    res = G.batch(qs[:10])
+    keep = res[7]
+    want = oracle.enumerate_rows(O, qs[7])
+    for i, r in enumerate(res):
+        if i != 7:
+            r.close()
+    del res
+    assert np.array_equal(oracle.sort_rows(keep.rows()), want)
