@@ -355,6 +355,95 @@ def cpu_baseline(queries, g) -> dict:
                       f"{emb} embeddings enumerated in {el:.1f} s"}
 
 
+# ----------------------------------------------------------------- served arm
+def run_served(args) -> dict:
+    """Poisson arrivals against two servers on the same resident graph: the plain
+    FIFO server (one slot, one query at a time) and the continuous-batching server
+    (slots that each take every pending request as one batch)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1906_03420_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS["served"]
+    g = synth.workload_graph("served")
+    nq = min(args.served_queries, w.n_queries)
+    queries = synth.queries("served", nq)
+    G = pkg.Graph.from_synth(g)
+    budget = int((args.budget_gb or 64) * (1 << 30))
+
+    def make(kind):
+        if kind == "plain":
+            return pkg.Server(G, mem_budget=budget, n_streams=1, max_batch=1)
+        return pkg.Server(G, mem_budget=budget, n_streams=args.served_slots, max_batch=0)
+
+    def closed_loop(kind):
+        S = make(kind)
+        for q in queries[: min(64, nq)]:                     # warm-up
+            S.poll(S.submit(q), -1)[0].close()
+        t0 = time.perf_counter()
+        tickets = [S.submit(q) for q in queries]
+        emb = 0
+        for t in tickets:
+            r, _ = S.poll(t, -1)
+            emb += r.count
+            r.close()
+        el = time.perf_counter() - t0
+        S.close()
+        return nq / el, emb / el
+
+    def open_loop(kind, rate):
+        arrivals = synth.poisson_arrivals(3000, nq, rate)
+        S = make(kind)
+        tickets = [None] * nq
+        lat = np.zeros(nq)
+        emb = [0]
+        done_at = [0.0]
+
+        def collect():
+            for i in range(nq):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                r, l = S.poll(tickets[i], -1)
+                lat[i] = l
+                emb[0] += r.count
+                r.close()
+            done_at[0] = time.perf_counter()
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for i, q in enumerate(queries):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = S.submit(q)
+        th.join()
+        S.close()
+        el = done_at[0] - t0
+        return {"rate": rate, "achieved_qps": nq / el, "embeddings_per_s": emb[0] / el,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    cap_plain, emb_plain = closed_loop("plain")
+    cap_batch, emb_batch = closed_loop("batched")
+    rates = [f * cap_plain for f in (0.5, 1.0, 2.0, 4.0)]
+    sweep = {"plain": [open_loop("plain", r) for r in rates], "batched": [open_loop("batched", r) for r in rates]}
+    slo = sweep["plain"][0]["p99_ms"]
+    best = {k: max([x["achieved_qps"] for x in v if x["p99_ms"] <= slo] or [0.0]) for k, v in sweep.items()}
+    return {"metric": METRIC, "value": best["batched"], "unit": "queries/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic (seeded R-MAT graph, random-walk queries, Poisson arrivals)",
+            "config": {"workload": "served", "graph": f"rmat n={w.graph.n} m={w.graph.m}",
+                       "queries": f"first {nq} of the {w.n_queries}-query stream", "k_range": [w.k_lo, w.k_hi],
+                       "query_admission_bound": w.max_bound, "slots": args.served_slots,
+                       "memory_budget_bytes": budget},
+            "closed_loop": {"plain": {"queries_per_s": cap_plain, "embeddings_per_s": emb_plain},
+                            "batched": {"queries_per_s": cap_batch, "embeddings_per_s": emb_batch}},
+            "latency_slo_ms": slo, "queries_per_s_at_slo": best, "sweep": sweep, "mode": "served"}
+
+
 # --------------------------------------------------------------- reference arm
 def run_reference(args) -> dict:
     import oracle
@@ -406,6 +495,8 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"],
                     help="plain: one query at a time; batched: one gsi_batch_run per step (auto: by workload)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    ap.add_argument("--served-queries", type=int, default=1000, help="prefix of the served arrival stream")
+    ap.add_argument("--served-slots", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -418,6 +509,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if args.workload == "served" and args.impl == "gsi":
+        if rank == 0:
+            print(json.dumps(run_served(args)), flush=True)
         return
 
     if world > 1:

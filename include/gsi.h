@@ -264,13 +264,22 @@ gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, con
 
 /* ---------------------------------------------------------------- served */
 typedef struct {
-    uint64_t mem_budget;     /* bytes for intermediate tables of admitted queries */
-    int32_t n_streams;       /* concurrent streams (slots) */
+    uint64_t mem_budget;     /* bytes for intermediate tables, split evenly over
+                                the slots; 0 = 40% of the device's memory */
+    int32_t n_streams;       /* slots: worker threads, each with its own stream
+                                (0 = 2) */
     uint64_t row_cap;        /* per query */
     int32_t count_only;
+    int32_t max_batch;       /* requests a slot takes at once (0 = all pending);
+                                1 = one query at a time on the plain path */
 } gsi_server_opts;
 
-/* A serving loop over a resident graph (continuous batching). */
+/*
+ * A serving loop over a resident graph (continuous batching): each slot takes
+ * every pending request, up to max_batch, as one batch and runs it on its own
+ * stream within its memory share, so requests arriving while other batches
+ * are on the GPU join the next free slot and slots overlap on the device.
+ */
 gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opts, gsi_server **out);
 /* Enqueue a query (copied).  *ticket identifies it in gsi_server_poll. */
 gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, uint64_t *ticket);
@@ -286,6 +295,16 @@ gsi_status gsi_server_cancel(gsi_server *s, uint64_t ticket);
 void gsi_server_destroy(gsi_server *s);
 
 /* ------------------------------------------------------------------ misc */
+/*
+ * Self-test of the library's bounded device waits (no counterpart in the
+ * paper): launches the grid barrier used by the one-launch query kernel with
+ * one CTA fewer than it waits for, so every wait must give up after
+ * spin_limit sleeps (0 = 4096) and the kernel must return.  Returns
+ * GSI_ETIMEOUT when the kernel reported the expired wait (the expected
+ * outcome), GSI_OK if it did not, GSI_ECUDA on launch failure.
+ */
+gsi_status gsi_selftest_wait_timeout(int32_t device, uint64_t spin_limit, double *elapsed_ms);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *gsi_last_error(void);
 /* Library version string. */

@@ -347,4 +347,11 @@ gsi_status gsi_plan_order(int32_t k, const int32_t *qsrc, const int32_t *qdst, c
     GSI_API_END
 }
 
+gsi_status gsi_selftest_wait_timeout(int32_t device, uint64_t spin_limit, double *elapsed_ms) {
+    GSI_API_BEGIN
+    GSI_TRY(prepare_device(device));
+    return selftest_barrier_timeout(device, spin_limit ? spin_limit : 4096, elapsed_ms);
+    GSI_API_END
+}
+
 }  // extern "C"

@@ -6,6 +6,8 @@
 // 1..15.  For each query vertex u the warp's 32 verdicts become one bitmap
 // word of C(u) through __ballot_sync, so C(u) is written directly in the
 // bitset form the join probes (Sec. V, "GPU-friendly set operation").
+#include <vector>
+
 #include "internal.h"
 #include "scan.cuh"
 
@@ -55,6 +57,42 @@ __global__ void __launch_bounds__(FNT) k_filter(const __grid_constant__ FilterAr
     if (lane < a.k && mycnt) atomicAdd(&cnt[lane], mycnt);
     __syncthreads();
     if (threadIdx.x < a.k && cnt[threadIdx.x]) atomicAdd(&a.counts[threadIdx.x], cnt[threadIdx.x]);
+}
+
+// All query vertices of a batch in one pass over the signature table: each
+// warp reads the 16 words of its 32 data vertices once and tests every query
+// vertex against them.  Bitmaps must be zeroed; only non-empty words are
+// written.
+__global__ void __launch_bounds__(FNT) k_filter_batch(const uint32_t *__restrict__ sig, int32_t n, int32_t nwords,
+                                                      const uint32_t *__restrict__ qsig, int32_t nqv,
+                                                      uint32_t *__restrict__ bitmaps,
+                                                      unsigned long long *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (FNT / 32);
+    for (int64_t grp = (int64_t)blockIdx.x * (FNT / 32) + (threadIdx.x >> 5); grp < nwords; grp += warps) {
+        const int64_t v = grp * 32 + lane;
+        const bool valid = v < n;
+        const uint32_t lab = valid ? __ldg(sig + v) : 0xffffffffu;
+        uint32_t w[GSI_SIG_WORDS];
+#pragma unroll
+        for (int j = 1; j < GSI_SIG_WORDS; ++j) w[j] = valid ? __ldg(sig + (int64_t)j * n + v) : 0u;
+        for (int32_t u = 0; u < nqv; ++u) {
+            const uint32_t *q = qsig + (int64_t)u * GSI_SIG_WORDS;
+            const uint32_t ql = __ldg(q);
+            bool pass = valid && lab == ql;
+            if (!__any_sync(FULL_MASK, pass)) continue;
+#pragma unroll
+            for (int j = 1; j < GSI_SIG_WORDS; ++j) {
+                const uint32_t qw = __ldg(q + j);
+                pass = pass && ((w[j] & qw) == qw);
+            }
+            const unsigned b = __ballot_sync(FULL_MASK, pass);
+            if (b && lane == 0) {
+                bitmaps[(int64_t)u * nwords + grp] = b;
+                atomicAdd(&counts[u], (unsigned long long)__popc(b));
+            }
+        }
+    }
 }
 
 struct PopcProducer {
@@ -116,6 +154,27 @@ gsi_status launch_filter(const gsi_graph *g, const QuerySig &q, uint32_t *bitmap
     if (blocks < 1) blocks = 1;
     k_filter<<<(unsigned)blocks, FNT, 0, st>>>(a);
     GSI_CUDA_TRY(cudaGetLastError());
+    return GSI_OK;
+}
+
+gsi_status launch_filter_batch(const gsi_graph *g, const std::vector<QuerySig> &qs, uint32_t *bitmaps,
+                               unsigned long long *counts, cudaStream_t st) {
+    std::vector<uint32_t> flat;
+    for (const QuerySig &q : qs)
+        for (int u = 0; u < q.k; ++u) flat.insert(flat.end(), q.sig[u], q.sig[u] + GSI_SIG_WORDS);
+    const int32_t nqv = (int32_t)(flat.size() / GSI_SIG_WORDS);
+    if (nqv == 0) return GSI_OK;
+    uint32_t *d_q = nullptr;
+    GSI_CUDA_TRY(cudaMallocAsync(&d_q, flat.size() * 4, st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(d_q, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, st));
+    GSI_CUDA_TRY(cudaMemsetAsync(bitmaps, 0, (size_t)nqv * (size_t)g->nwords * 4, st));
+    GSI_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)nqv * 8, st));
+    int64_t blocks = ((int64_t)g->nwords + (FNT / 32) - 1) / (FNT / 32);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_filter_batch<<<(unsigned)blocks, FNT, 0, st>>>(g->sig, g->n, g->nwords, d_q, nqv, bitmaps, counts);
+    GSI_CUDA_TRY(cudaGetLastError());
+    cudaFreeAsync(d_q, st);
     return GSI_OK;
 }
 

@@ -49,6 +49,10 @@ void query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, cons
 // bitmaps: device uint32[k][nwords]; counts: device unsigned long long[k] (zeroed here).
 gsi_status launch_filter(const gsi_graph *g, const QuerySig &q, uint32_t *bitmaps, unsigned long long *counts,
                          cudaStream_t st);
+// Every query vertex of a batch in one pass: bitmaps [sum k][nwords] and
+// counts [sum k] in query order (zeroed here).
+gsi_status launch_filter_batch(const gsi_graph *g, const std::vector<QuerySig> &qs, uint32_t *bitmaps,
+                               unsigned long long *counts, cudaStream_t st);
 // Compact the bitmap of C(u) into the int32 list out (ascending); scratch: uint32[scan_blocks+1].
 gsi_status launch_seed(const gsi_graph *g, const uint32_t *bitmap, int32_t *out, uint32_t *scratch,
                        cudaStream_t st);
@@ -105,9 +109,14 @@ struct QueryCtl {
     unsigned bar_count, bar_gen;
     unsigned fail;        // 1 scratch too small, 2 table overflow, 4 barrier wait gave up
     unsigned pad;
+    unsigned long long spin_limit;   // sleeps before a barrier wait gives up (0 = default)
 };
 constexpr int QUERY_MAX_CTAS = 1024;
 size_t join_args_size();
+// Self-test of the bounded grid barrier: a cooperative launch whose barrier
+// expects one CTA more than it has, so every wait must run out.  Returns
+// GSI_ETIMEOUT when the kernel reported that, GSI_OK otherwise.
+gsi_status selftest_barrier_timeout(int dev, unsigned long long spin_limit, double *ms);
 // Seed + every join step of one query in one cooperative launch.  cfg_dev:
 // join_args_size() * k bytes; dsteps: k records (host-initialised static
 // fields); bsum: QUERY_MAX_CTAS words.  steps[0].count receives |seed|.

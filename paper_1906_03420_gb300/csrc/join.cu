@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(NT) k_join(const __grid_constant__ JoinArgs a)
 constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 24;   // x ~64 ns sleeps: about a second
 
 __device__ __forceinline__ bool grid_barrier(QueryCtl *ctl, unsigned nblocks) {
+    const unsigned long long limit = ctl->spin_limit ? ctl->spin_limit : BARRIER_SPIN_LIMIT;
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -129,7 +130,7 @@ __device__ __forceinline__ bool grid_barrier(QueryCtl *ctl, unsigned nblocks) {
             unsigned long long spins = 0;
             while (*gen == g) {
                 if (*fail & 4u) { ok = 0; break; }
-                if (++spins > BARRIER_SPIN_LIMIT) {
+                if (++spins > limit) {
                     atomicOr(&ctl->fail, 4u);
                     ok = 0;
                     break;
@@ -282,6 +283,11 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
     }
 }
 
+__global__ void k_barrier_selftest(QueryCtl *ctl, unsigned expect) {
+    // every CTA waits at a barrier that expects one CTA more than exist
+    grid_barrier(ctl, expect);
+}
+
 int g_smem_set[64];
 
 StepDev step_dev(const gsi_graph *g, const JoinStep &s) {
@@ -423,6 +429,46 @@ gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &st
                     (void *)&bsum};
     GSI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_query<JOIN_NT, JOIN_VT>, dim3(grid), dim3(JOIN_NT), args,
                                              sm, st));
+    return GSI_OK;
+}
+
+gsi_status selftest_barrier_timeout(int dev, unsigned long long spin_limit, double *ms) {
+    GSI_CUDA_TRY(cudaSetDevice(dev));
+    QueryCtl *ctl = nullptr;
+    GSI_CUDA_TRY(cudaMalloc(&ctl, sizeof(QueryCtl)));
+    QueryCtl h;
+    std::memset(&h, 0, sizeof h);
+    h.spin_limit = spin_limit;
+    gsi_status rc = GSI_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    if (cudaMemcpy(ctl, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) rc = GSI_ECUDA;
+    const unsigned grid = 8;
+    unsigned expect = grid + 1;
+    void *args[] = {(void *)&ctl, (void *)&expect};
+    if (rc == GSI_OK) {
+        cudaEventRecord(e0, 0);
+        if (cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(grid), dim3(JOIN_NT), args, 0, 0) !=
+            cudaSuccess)
+            rc = GSI_ECUDA;
+        cudaEventRecord(e1, 0);
+    }
+    if (rc == GSI_OK && cudaMemcpy(&h, ctl, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) rc = GSI_ECUDA;
+    float t = 0;
+    if (rc == GSI_OK) cudaEventElapsedTime(&t, e0, e1);
+    if (ms) *ms = t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ctl);
+    if (rc != GSI_OK) {
+        set_error("barrier self-test: launch or copy failed");
+        return rc;
+    }
+    if (h.fail & 4u) {
+        set_error("barrier self-test: the wait ran out as intended");
+        return GSI_ETIMEOUT;
+    }
     return GSI_OK;
 }
 

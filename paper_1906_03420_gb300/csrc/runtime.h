@@ -101,6 +101,8 @@ struct BatchPlan {
 };
 
 gsi_status plan_for_batch(gsi_graph *g, BatchPlan &p, const uint64_t *cand_counts, const int32_t *ranks);
+gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
+                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses);
 gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o, uint64_t budget,
                             cudaStream_t st, gsi_stats *stats);
 gsi_status prepare_device(int dev);

@@ -19,6 +19,147 @@ using namespace gsi;
 // one filter launch per query, one readback of every |C(u)|, host plans, then
 // the batch kernel.  Queries whose tables did not fit the batch arena run
 // again on the plain path.
+// Batched queries (a shared work queue in one persistent launch, batch.cu):
+// one filter pass for every query vertex of the batch, one readback of every
+// |C(u)|, host plans, then the batch kernel.  Queries whose tables did not fit
+// the batch arena run again on the plain path.  Invalid queries carry their
+// status in plans[i].status.
+namespace gsi {
+gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
+                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses) {
+    const int32_t nq = (int32_t)plans.size();
+    outs.assign((size_t)nq, nullptr);
+    statuses.assign((size_t)nq, GSI_OK);
+    GSI_TRY(prepare_device(g->device));
+    cudaStream_t st = (cudaStream_t)bo.stream;
+    uint64_t budget = bo.mem_budget;
+    if (!budget) {
+        size_t fr = 0, tot = 0;
+        GSI_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        budget = (uint64_t)(0.4 * (double)tot);
+    }
+    std::vector<int32_t> ranks((size_t)nq * GSI_MAX_QUERY_VERTICES, 0);
+    uint64_t bm_words = 0, nk = 0;
+    std::vector<uint64_t> bm_off((size_t)nq, 0), k_off((size_t)nq, 0);
+    for (int32_t i = 0; i < nq; ++i) {
+        BatchPlan &p = plans[i];
+        if (p.status != GSI_OK) continue;
+        p.k = p.q.k;
+        bool empty = (p.k > 1 && g->m == 0);
+        for (int e = 0; e < p.q.qm && !empty; ++e) empty |= p.q.lab[e] >= g->L || g->freq[p.q.lab[e]] == 0;
+        for (int u = 0; u < p.k && !empty; ++u) {
+            ranks[(size_t)i * GSI_MAX_QUERY_VERTICES + u] = g->label_rank(p.q.vlab[u]);
+            empty |= ranks[(size_t)i * GSI_MAX_QUERY_VERTICES + u] < 0;
+        }
+        if (empty) continue;
+        p.active = true;
+        bm_off[i] = bm_words;
+        k_off[i] = nk;
+        bm_words += (uint64_t)p.k * (uint64_t)g->nwords;
+        nk += (uint64_t)p.k;
+    }
+    uint32_t *bitmaps = nullptr;
+    unsigned long long *counts = nullptr;
+    if (nk) {
+        GSI_CUDA_TRY(cudaMallocAsync(&bitmaps, bm_words * 4 + 16, st));
+        GSI_CUDA_TRY(cudaMallocAsync(&counts, nk * 8, st));
+    }
+    gsi_status rc = GSI_OK;
+    cudaEvent_t f0 = nullptr, f1 = nullptr;
+    if (bo.stats) {
+        cudaEventCreate(&f0);
+        cudaEventCreate(&f1);
+        cudaEventRecord(f0, st);
+    }
+    uint64_t nfilters = 0;
+    {
+        std::vector<QuerySig> sigs;
+        for (int32_t i = 0; i < nq; ++i) {
+            BatchPlan &p = plans[i];
+            if (!p.active) continue;
+            sigs.emplace_back();
+            query_signatures(p.q.vl.data(), p.k, p.q.src.data(), p.q.dst.data(), p.q.lab.data(), p.q.qm,
+                             &sigs.back());
+            p.bitmaps = bitmaps + bm_off[i];
+        }
+        if (!sigs.empty()) {
+            rc = launch_filter_batch(g, sigs, bitmaps, counts, st);
+            nfilters = 1;
+        }
+    }
+    if (bo.stats) cudaEventRecord(f1, st);
+    std::vector<uint64_t> hc(nk);
+    if (rc == GSI_OK && nk) {
+        if (cudaMemcpyAsync(hc.data(), counts, nk * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("batch: filter readback failed");
+            rc = GSI_ECUDA;
+        }
+    }
+    if (bo.stats && f0) {
+        float ms = 0;
+        if (rc == GSI_OK) cudaEventElapsedTime(&ms, f0, f1);
+        bo.stats->filter_ms += ms;
+        bo.stats->filter_launches += nfilters;
+        bo.stats->kernels += nfilters;
+        bo.stats->filter_bytes += nfilters * ((uint64_t)g->n * 64 + bm_words * 4);
+        cudaEventDestroy(f0);
+        cudaEventDestroy(f1);
+    }
+    for (int32_t i = 0; i < nq && rc == GSI_OK; ++i) {
+        BatchPlan &p = plans[i];
+        if (!p.active) continue;
+        const uint64_t *c = hc.data() + k_off[i];
+        bool empty = false;
+        for (int u = 0; u < p.k; ++u) empty |= c[u] == 0;
+        if (empty) {
+            p.active = false;
+            continue;
+        }
+        plan_for_batch(g, p, c, ranks.data() + (size_t)i * GSI_MAX_QUERY_VERTICES);
+    }
+    if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats);
+    if (bitmaps) cudaFreeAsync(bitmaps, st);
+    if (counts) cudaFreeAsync(counts, st);
+    if (rc != GSI_OK) return rc;
+    gsi_status first_err = GSI_OK;
+    for (int32_t i = 0; i < nq; ++i) {
+        BatchPlan &p = plans[i];
+        gsi_status qrc = p.status;
+        if (qrc == GSI_OK && p.active && p.failed) {
+            gsi_query_opts o;
+            std::memset(&o, 0, sizeof o);
+            o.stream = bo.stream;
+            o.row_cap = bo.row_cap;
+            o.mem_budget = budget;
+            o.count_only = bo.count_only;
+            o.stats = bo.stats;
+            qrc = run_query(g, p.q, o, &outs[i]);
+            if (bo.stats) bo.stats->host_driven += 1;
+        } else if (qrc == GSI_OK) {
+            gsi_result *r = new gsi_result();
+            r->k = p.k;
+            r->device = g->device;
+            r->count = p.active ? p.count : 0;
+            uint64_t keep = bo.count_only ? 0 : (bo.row_cap ? bo.row_cap : UINT64_MAX);
+            for (auto &c : p.chunks) {
+                if (r->materialised >= keep) break;
+                gsi_result::Chunk ch = c;
+                ch.nrows = std::min<uint64_t>(ch.nrows, keep - r->materialised);
+                ch.owned = false;
+                r->chunks.push_back(ch);
+                r->materialised += ch.nrows;
+            }
+            r->arena = p.arena;
+            outs[i] = r;
+        }
+        statuses[i] = qrc;
+        if (qrc != GSI_OK && qrc != GSI_EINVAL && first_err == GSI_OK) first_err = qrc;
+    }
+    return first_err;
+}
+}  // namespace gsi
+
 extern "C" gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
                                     gsi_result **outs, int32_t *statuses) {
     if (!g || (nq > 0 && (!qs || !outs)) || nq < 0) {
@@ -29,130 +170,18 @@ extern "C" gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int3
         gsi_batch_opts bo;
         std::memset(&bo, 0, sizeof bo);
         if (opts) bo = *opts;
-        GSI_TRY(prepare_device(g->device));
-        cudaStream_t st = (cudaStream_t)bo.stream;
-        uint64_t budget = bo.mem_budget;
-        if (!budget) {
-            size_t fr = 0, tot = 0;
-            GSI_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-            budget = (uint64_t)(0.4 * (double)tot);
-        }
         std::vector<BatchPlan> plans((size_t)nq);
-        std::vector<int32_t> ranks((size_t)nq * GSI_MAX_QUERY_VERTICES, 0);
-        uint64_t bm_words = 0, nk = 0;
-        std::vector<uint64_t> bm_off((size_t)nq, 0), k_off((size_t)nq, 0);
+        for (int32_t i = 0; i < nq; ++i)
+            plans[i].status = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm,
+                                             &plans[i].q);
+        std::vector<gsi_result *> res;
+        std::vector<gsi_status> sts;
+        gsi_status rc = batch_execute(g, plans, bo, res, sts);
         for (int32_t i = 0; i < nq; ++i) {
-            outs[i] = nullptr;
-            BatchPlan &p = plans[i];
-            p.status = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm, &p.q);
-            if (p.status != GSI_OK) continue;
-            p.k = p.q.k;
-            bool empty = (p.k > 1 && g->m == 0);
-            for (int e = 0; e < p.q.qm && !empty; ++e)
-                empty |= p.q.lab[e] >= g->L || g->freq[p.q.lab[e]] == 0;
-            for (int u = 0; u < p.k && !empty; ++u) {
-                ranks[(size_t)i * GSI_MAX_QUERY_VERTICES + u] = g->label_rank(p.q.vlab[u]);
-                empty |= ranks[(size_t)i * GSI_MAX_QUERY_VERTICES + u] < 0;
-            }
-            if (empty) continue;
-            p.active = true;
-            bm_off[i] = bm_words;
-            k_off[i] = nk;
-            bm_words += (uint64_t)p.k * (uint64_t)g->nwords;
-            nk += (uint64_t)p.k;
+            outs[i] = i < (int32_t)res.size() ? res[i] : nullptr;
+            if (statuses) statuses[i] = i < (int32_t)sts.size() ? sts[i] : rc;
         }
-        uint32_t *bitmaps = nullptr;
-        unsigned long long *counts = nullptr;
-        if (nk) {
-            GSI_CUDA_TRY(cudaMallocAsync(&bitmaps, bm_words * 4 + 16, st));
-            GSI_CUDA_TRY(cudaMallocAsync(&counts, nk * 8, st));
-        }
-        gsi_status rc = GSI_OK;
-        cudaEvent_t f0 = nullptr, f1 = nullptr;
-        if (bo.stats) {
-            cudaEventCreate(&f0);
-            cudaEventCreate(&f1);
-            cudaEventRecord(f0, st);
-        }
-        uint64_t nfilters = 0;
-        for (int32_t i = 0; i < nq && rc == GSI_OK; ++i) {
-            BatchPlan &p = plans[i];
-            if (!p.active) continue;
-            QuerySig sig;
-            query_signatures(p.q.vl.data(), p.k, p.q.src.data(), p.q.dst.data(), p.q.lab.data(), p.q.qm, &sig);
-            p.bitmaps = bitmaps + bm_off[i];
-            rc = launch_filter(g, sig, bitmaps + bm_off[i], counts + k_off[i], st);
-            ++nfilters;
-        }
-        if (bo.stats) cudaEventRecord(f1, st);
-        std::vector<uint64_t> hc(nk);
-        if (rc == GSI_OK && nk) {
-            if (cudaMemcpyAsync(hc.data(), counts, nk * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess) {
-                set_error("gsi_batch_run: filter readback failed");
-                rc = GSI_ECUDA;
-            }
-        }
-        if (bo.stats && f0) {
-            float ms = 0;
-            if (rc == GSI_OK) cudaEventElapsedTime(&ms, f0, f1);
-            bo.stats->filter_ms += ms;
-            bo.stats->filter_launches += nfilters;
-            bo.stats->kernels += nfilters;
-            bo.stats->filter_bytes += nfilters * ((uint64_t)g->n * 64);
-            cudaEventDestroy(f0);
-            cudaEventDestroy(f1);
-        }
-        for (int32_t i = 0; i < nq && rc == GSI_OK; ++i) {
-            BatchPlan &p = plans[i];
-            if (!p.active) continue;
-            const uint64_t *c = hc.data() + k_off[i];
-            bool empty = false;
-            for (int u = 0; u < p.k; ++u) empty |= c[u] == 0;
-            if (empty) {
-                p.active = false;
-                continue;
-            }
-            plan_for_batch(g, p, c, ranks.data() + (size_t)i * GSI_MAX_QUERY_VERTICES);
-        }
-        if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats);
-        if (bitmaps) cudaFreeAsync(bitmaps, st);
-        if (counts) cudaFreeAsync(counts, st);
-        if (rc != GSI_OK) return rc;
-        gsi_status first_err = GSI_OK;
-        for (int32_t i = 0; i < nq; ++i) {
-            BatchPlan &p = plans[i];
-            gsi_status qrc = p.status;
-            if (qrc == GSI_OK && p.active && p.failed) {
-                gsi_query_opts o;
-                std::memset(&o, 0, sizeof o);
-                o.stream = bo.stream;
-                o.row_cap = bo.row_cap;
-                o.count_only = bo.count_only;
-                o.stats = bo.stats;
-                qrc = run_query(g, p.q, o, &outs[i]);
-                if (bo.stats) bo.stats->host_driven += 1;
-            } else if (qrc == GSI_OK) {
-                gsi_result *r = new gsi_result();
-                r->k = p.k;
-                r->device = g->device;
-                r->count = p.active ? p.count : 0;
-                uint64_t keep = bo.row_cap ? bo.row_cap : UINT64_MAX;
-                for (auto &c : p.chunks) {
-                    if (r->materialised >= keep) break;
-                    gsi_result::Chunk ch = c;
-                    ch.nrows = std::min<uint64_t>(ch.nrows, keep - r->materialised);
-                    ch.owned = false;
-                    r->chunks.push_back(ch);
-                    r->materialised += ch.nrows;
-                }
-                r->arena = p.arena;
-                outs[i] = r;
-            }
-            if (statuses) statuses[i] = qrc;
-            if (qrc != GSI_OK && qrc != GSI_EINVAL && first_err == GSI_OK) first_err = qrc;
-        }
-        return first_err;
+        return rc;
     } catch (const std::bad_alloc &) {
         set_error("gsi_batch_run: host allocation failed");
         return GSI_ENOMEM;
@@ -182,37 +211,69 @@ struct gsi_server {
     std::vector<cudaStream_t> streams;
 };
 
+// One slot: a worker thread with its own stream and an equal share of the
+// memory budget.  It takes every pending request (up to max_batch) as one
+// batch, so requests that arrived while other batches were on the GPU are
+// admitted as soon as a slot frees; batches of different slots overlap on
+// the device.  With max_batch == 1 a slot runs one query at a time on the
+// plain path.
 static void server_worker(gsi_server *s, int idx) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = s->streams[idx];
+    const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
+    const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
     for (;;) {
-        std::shared_ptr<gsi_server::Req> r;
+        std::vector<std::shared_ptr<gsi_server::Req>> batch;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
             if (s->stop && s->queue.empty()) return;
-            r = s->queue.front();
-            s->queue.pop_front();
-            if (r->cancelled) {
-                r->status = GSI_ECANCELLED;
-                s->cv_done.notify_all();
-                continue;
+            while (!s->queue.empty() && batch.size() < max_batch) {
+                auto r = s->queue.front();
+                s->queue.pop_front();
+                if (r->cancelled) {
+                    r->status = GSI_ECANCELLED;
+                    continue;
+                }
+                batch.push_back(r);
             }
         }
-        gsi_query_opts o;
-        std::memset(&o, 0, sizeof o);
-        o.stream = st;
-        o.row_cap = s->opts.row_cap;
-        o.count_only = s->opts.count_only;
-        o.mem_budget = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
-        gsi_result *res = nullptr;
-        gsi_status rc = run_query(s->g, r->q, o, &res);
+        if (batch.empty()) {
+            s->cv_done.notify_all();
+            continue;
+        }
+        std::vector<gsi_result *> res(batch.size(), nullptr);
+        std::vector<gsi_status> sts(batch.size(), GSI_OK);
+        if (batch.size() == 1 && max_batch == 1) {
+            gsi_query_opts o;
+            std::memset(&o, 0, sizeof o);
+            o.stream = st;
+            o.row_cap = s->opts.row_cap;
+            o.count_only = s->opts.count_only;
+            o.mem_budget = share;
+            sts[0] = run_query(s->g, batch[0]->q, o, &res[0]);
+        } else {
+            std::vector<BatchPlan> plans(batch.size());
+            for (size_t i = 0; i < batch.size(); ++i) plans[i].q = batch[i]->q;
+            gsi_batch_opts bo;
+            std::memset(&bo, 0, sizeof bo);
+            bo.stream = st;
+            bo.row_cap = s->opts.row_cap;
+            bo.mem_budget = share;
+            bo.count_only = s->opts.count_only;
+            gsi_status rc = batch_execute(s->g, plans, bo, res, sts);
+            if (rc != GSI_OK)
+                for (size_t i = 0; i < batch.size(); ++i)
+                    if (sts[i] == GSI_OK && !res[i]) sts[i] = rc;
+        }
         auto now = std::chrono::steady_clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            r->res = res;
-            r->status = rc;
-            r->latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+            for (size_t i = 0; i < batch.size(); ++i) {
+                batch[i]->res = res[i];
+                batch[i]->status = sts[i];
+                batch[i]->latency_ms = std::chrono::duration<double, std::milli>(now - batch[i]->t_submit).count();
+            }
         }
         s->cv_done.notify_all();
     }
@@ -228,7 +289,7 @@ extern "C" gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opt
     s->g = g;
     std::memset(&s->opts, 0, sizeof s->opts);
     if (opts) s->opts = *opts;
-    if (s->opts.n_streams < 1) s->opts.n_streams = 4;
+    if (s->opts.n_streams < 1) s->opts.n_streams = 2;
     if (s->opts.mem_budget == 0) {
         size_t fr = 0, tot = 0;
         GSI_CUDA_TRY(cudaMemGetInfo(&fr, &tot));

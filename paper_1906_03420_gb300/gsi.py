@@ -27,7 +27,7 @@ EXPORTED = [
     "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_destroy",
     "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_join_step_noalloc", "gsi_plan_order",
     "gsi_batch_run", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
-    "gsi_server_destroy", "gsi_last_error", "gsi_version",
+    "gsi_server_destroy", "gsi_last_error", "gsi_version", "gsi_selftest_wait_timeout",
 ]
 
 
@@ -83,7 +83,7 @@ class c_batch_opts(ctypes.Structure):
 
 class c_server_opts(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_uint64), ("n_streams", ctypes.c_int32), ("row_cap", ctypes.c_uint64),
-                ("count_only", ctypes.c_int32)]
+                ("count_only", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
 
 
 _lib = None
@@ -160,6 +160,8 @@ def load(build_if_missing: bool = False):
     L.gsi_server_destroy.restype = None
     L.gsi_last_error.argtypes = []
     L.gsi_last_error.restype = ctypes.c_char_p
+    L.gsi_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+    L.gsi_selftest_wait_timeout.restype = st
     L.gsi_version.argtypes = []
     L.gsi_version.restype = ctypes.c_char_p
     _lib = L
@@ -398,11 +400,11 @@ def plan_order(q, cand, freq) -> tuple[np.ndarray, np.ndarray]:
 class Server:
     """Continuous-batching server over a resident graph (gsi_server_*)."""
 
-    def __init__(self, graph: Graph, mem_budget: int = 0, n_streams: int = 4, row_cap: int = 0,
-                 count_only: bool = False):
+    def __init__(self, graph: Graph, mem_budget: int = 0, n_streams: int = 2, row_cap: int = 0,
+                 count_only: bool = False, max_batch: int = 0):
         self._graph = graph
         h = VP()
-        o = c_server_opts(mem_budget, n_streams, row_cap, int(count_only))
+        o = c_server_opts(mem_budget, n_streams, row_cap, int(count_only), max_batch)
         _check(load().gsi_server_create(graph.handle, ctypes.byref(o), ctypes.byref(h)), "gsi_server_create")
         self._h = h.value
 
@@ -433,6 +435,13 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def selftest_wait_timeout(device: int = 0, spin_limit: int = 4096) -> tuple[int, float]:
+    """Run the bounded-wait self-test; returns (status, elapsed ms); GSI_ETIMEOUT is the expected status."""
+    ms = ctypes.c_double()
+    rc = load().gsi_selftest_wait_timeout(device, spin_limit, ctypes.byref(ms))
+    return int(rc), float(ms.value)
 
 
 def version() -> str:
