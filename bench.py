@@ -195,9 +195,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                 stats_list.append(st)
         return total
 
+    tuned = {}
+    if batched:
+        spi, ms = pkg.batch_autotune(G, mine[:512], stream=stream, mem_budget=budget)
+        tuned = {"seeds_per_item": spi, "calibration_ms": ms, "calibration_queries": min(512, len(mine))}
+
     def batch_step(stats_list=None):
         st = pkg.c_stats() if stats_list is not None else None
-        res = G.batch(mine, stream=stream, row_cap=row_cap, mem_budget=budget, stats=st)
+        res = G.batch(mine, stream=stream, row_cap=row_cap, mem_budget=budget, stats=st,
+                      seeds_per_item=tuned.get("seeds_per_item", 0))
         total = 0
         for r in res:
             if isinstance(r, Exception):
@@ -283,7 +289,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             if batched:
-                res = G.batch(mine, stream=stream, row_cap=row_cap)
+                res = G.batch(mine, stream=stream, row_cap=row_cap, seeds_per_item=tuned.get("seeds_per_item", 0))
                 for q, r in zip(mine, res):
                     c = r.count
                     rows, _capped = r.copy_to(host.data_ptr(), c)
@@ -334,6 +340,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
            "filter": {"achieved_gbs": fb / (fms * 1e-3) / 1e9 if fms > 0 else None, "ms_per_step": fms / args.steps},
            "gpu_launches": int(allv[:, 8].sum()), "host_driven_queries": int(host_driven), "clocks": clocks,
            "e2e": e2e, "mode": "batched" if batched else "plain"}
+    if tuned:
+        out["autotuned"] = tuned
     if plain_cmp is not None:
         out["plain_path_same_queries"] = plain_cmp
     if args.cpu_baseline and rank == 0:
@@ -374,10 +382,12 @@ def run_served(args) -> dict:
     G = pkg.Graph.from_synth(g)
     budget = int((args.budget_gb or 64) * (1 << 30))
 
+    spi, _ = pkg.batch_autotune(G, queries[:256], mem_budget=budget // max(1, args.served_slots))
+
     def make(kind):
         if kind == "plain":
             return pkg.Server(G, mem_budget=budget, n_streams=1, max_batch=1)
-        return pkg.Server(G, mem_budget=budget, n_streams=args.served_slots, max_batch=0)
+        return pkg.Server(G, mem_budget=budget, n_streams=args.served_slots, max_batch=0, seeds_per_item=spi)
 
     def closed_loop(kind):
         S = make(kind)
@@ -438,6 +448,7 @@ def run_served(args) -> dict:
             "config": {"workload": "served", "graph": f"rmat n={w.graph.n} m={w.graph.m}",
                        "queries": f"first {nq} of the {w.n_queries}-query stream", "k_range": [w.k_lo, w.k_hi],
                        "query_admission_bound": w.max_bound, "slots": args.served_slots,
+                       "autotuned_seeds_per_item": spi,
                        "memory_budget_bytes": budget},
             "closed_loop": {"plain": {"queries_per_s": cap_plain, "embeddings_per_s": emb_plain},
                             "batched": {"queries_per_s": cap_batch, "embeddings_per_s": emb_batch}},

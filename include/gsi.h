@@ -151,9 +151,12 @@ typedef struct {
  * Find all embeddings of Q in G (Defs. 2-3): filter (Sec. III-A), order by
  * Alg. 2, then one join iteration per remaining query vertex (Alg. 3 with the
  * Alg. 4 upper bound on each row's output).  The steps run device-driven in
- * an arena of mem_budget bytes (one scratch and two table regions, sizes
- * kept on the device, no host wait between steps); if a table does not fit,
- * the query is redone host-driven with row ranges halved until each fits.
+ * an arena (one scratch and two table regions, sizes kept on the device, no
+ * host wait between steps) of min(mem_budget, 8 GiB) bytes; if a table does
+ * not fit, the query is redone with an arena four times larger, up to
+ * mem_budget, and past that host-driven, with row ranges halved until each
+ * fits.  (A single arena of the whole default budget costs milliseconds per
+ * query to reserve; most queries fit the first one.)
  *   qvlab int32[k]; query edges {qsrc[i], qdst[i]} with label qelab[i], i < qm.
  * Q must be connected (the paper assumes so, Sec. II-A), have 1 <= k <= 32
  * vertices, no self-loop and no repeated vertex pair: otherwise GSI_EINVAL.
@@ -175,6 +178,8 @@ gsi_status gsi_result_columns(const gsi_result *r, int32_t *k);
  * count (row cap or count-only), GSI_OK otherwise.
  */
 gsi_status gsi_result_copy(const gsi_result *r, int32_t *dst, uint64_t max_rows, uint64_t *rows);
+/* Releases the result's device memory stream-ordered on the stream it was
+   produced on: destroy results before destroying that stream. */
 void gsi_result_destroy(gsi_result *r);
 
 /* ------------------------------------------------------- step-level calls */
@@ -252,6 +257,11 @@ typedef struct {
     uint64_t mem_budget;     /* bytes for all intermediate tables of the batch */
     int32_t count_only;
     gsi_stats *stats;        /* optional, accumulated over the batch */
+    int32_t seeds_per_item;  /* work-item size: candidates of the first query
+                                vertex per (query, range) item; 0 = 32 */
+    int32_t item_rows;       /* a query whose item's table grows past this many
+                                rows leaves the batch and runs on the plain path
+                                (all SMs); 0 = only when the table does not fit */
 } gsi_batch_opts;
 
 /*
@@ -261,6 +271,15 @@ typedef struct {
  */
 gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
                          gsi_result **outs, int32_t *statuses);
+
+/*
+ * Autotuner for batched execution (no counterpart in the paper): runs the
+ * given calibration batch once per candidate work-item size (seeds_per_item
+ * in {16, 32, 64, 128, 256}), each twice, and returns the fastest in
+ * *best_seeds_per_item with its time in *best_ms (both optional).
+ */
+gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
+                              int32_t *best_seeds_per_item, double *best_ms);
 
 /* ---------------------------------------------------------------- served */
 typedef struct {
@@ -272,6 +291,13 @@ typedef struct {
     int32_t count_only;
     int32_t max_batch;       /* requests a slot takes at once (0 = all pending);
                                 1 = one query at a time on the plain path */
+    int32_t seeds_per_item;  /* batch work-item size (0 = 32); see
+                                gsi_batch_autotune */
+    int32_t item_rows;       /* see gsi_batch_opts.item_rows */
+    int32_t min_batch;       /* fewer pending requests than this run one at a
+                                time on the plain path (every step on all SMs:
+                                lower latency than a batch too small to fill
+                                the GPU); 0 = 8 */
 } gsi_server_opts;
 
 /*

@@ -1,6 +1,7 @@
 // extern "C" entry points of include/gsi.h.
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -9,12 +10,25 @@
 
 using namespace gsi;
 
+// Result memory is released stream-ordered on a library stream: cudaFree
+// would wait for every kernel on the device, stalling concurrent queries.
+// The producing stream has always completed before a result is handed out.
+static cudaStream_t release_stream(int dev) {
+    static std::mutex mu;
+    static cudaStream_t streams[64];
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
 gsi_result::~gsi_result() {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
+    cudaStream_t rs = own_stream ? stream : release_stream(device);
     for (auto &c : chunks)
-        if (c.owned) cudaFree(c.rows);
+        if (c.owned) cudaFreeAsync(c.rows, rs);
     arena.reset();
     if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }
@@ -24,7 +38,7 @@ gsi::ResultArena::~ResultArena() {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
-    cudaFree(ptr);
+    cudaFreeAsync(ptr, own_stream ? stream : release_stream(device));
     if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }
 

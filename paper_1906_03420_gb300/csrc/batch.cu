@@ -57,6 +57,7 @@ struct BatchArgs {
     unsigned long long *result_used;
     unsigned char *arena;          // per-CTA slices
     uint64_t slice_bytes, s_bytes, t_bytes;
+    uint64_t item_rows;            // an item whose table grows past this fails over (0 = region size)
 };
 
 __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs b) {
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
             }
             R = run;
         }
+        __syncthreads();               // step 1 reads seeds written by other threads
         int cur = 0;
         bool failed = false;
         uint64_t cap = 0;
@@ -148,10 +150,13 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
             __syncthreads();
             const uint64_t cnt = cnt_s;
             if (!last && cnt > cap) { failed = true; break; }
+            if (b.item_rows && cnt > b.item_rows) { failed = true; break; }
             R = cnt;
             cur ^= 1;
         }
         if (k == 1) cap = bq->count_only ? 0 : b.t_bytes / 4;
+        // the final table must also have fit (rows past the region are lost)
+        if (!failed && !bq->count_only && R > cap) failed = true;
         // ---- final rows to the result arena
         const uint64_t rows = failed ? 0 : min(R, cap);
         if (threadIdx.x == 0) {
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
 // Per-query plan for a batch: the host-side part of run_query (filter counts
 // already known), producing the steps of one query.
 gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o,
-                            uint64_t budget, cudaStream_t st, gsi_stats *stats) {
+                            uint64_t budget, cudaStream_t st, gsi_stats *stats, BatchWorkspace *ws) {
     const int nq = (int)plans.size();
     if (nq == 0) return GSI_OK;
     // device counters of algorithmic bytes and candidates (only with stats)
@@ -200,30 +205,9 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
     size_t sm = join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, 1, 1);
     for (int i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
-        std::memset(&bqs[i], 0, sizeof(BatchQuery));
-        bqs[i].k = p.k;
-        bqs[i].count_only = o.count_only;
         if (!p.active) continue;
-        bqs[i].seed_bm = p.bitmaps + (uint64_t)p.order[0] * (uint64_t)g->nwords;
-        for (int t = 1; t < p.k; ++t) {
-            const int co = (t == p.k - 1) && o.count_only;
-            cfg[(size_t)i * GSI_MAX_QUERY_VERTICES + t] =
-                make_join_args(g, p.steps[t], p.bitmaps + (uint64_t)p.order[t] * (uint64_t)g->nwords, co, dstats);
+        for (int t = 1; t < p.k; ++t)
             sm = std::max(sm, join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, p.steps[t].t, p.steps[t].d));
-        }
-        // split the seed bitmap into word ranges holding about 2^12 seeds each
-        const uint64_t nw = (uint64_t)g->nwords;
-        uint64_t parts = (p.seed_count + 4095) / 4096;
-        if (parts < 1) parts = 1;
-        if (parts > nw) parts = nw;
-        for (uint64_t j = 0; j < parts; ++j) {
-            BatchItem it;
-            it.q = i;
-            it.pad = 0;
-            it.word_lo = (int64_t)(nw * j / parts);
-            it.word_hi = (int64_t)(nw * (j + 1) / parts);
-            if (it.word_hi > it.word_lo) items.push_back(it);
-        }
     }
     if (sm > 200 * 1024) {
         set_error("batch: shared memory need exceeds 200 KB");
@@ -238,16 +222,50 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
         set_error("batch: kernel does not fit on an SM");
         return GSI_EINVAL;
     }
-    const int grid = nsm * per_sm;
-    // memory: result arena 40%, per-CTA slices 60% (scratch 20%, two tables 40% each)
-    const uint64_t align = 256;
-    uint64_t result_bytes = (budget * 2 / 5) / align * align;
-    uint64_t slice = ((budget - result_bytes) / (uint64_t)grid) / align * align;
-    uint64_t s_bytes = (slice / 5) / align * align;
-    uint64_t t_bytes = ((slice - s_bytes) / 2) / align * align;
-    if (t_bytes < (uint64_t)g->nwords * 32 * 4 + 1024) {
-        set_error("batch: memory budget too small for the per-CTA tables");
-        return GSI_ENOMEM;
+    // memory: result arena 40%, per-CTA slices 60% (scratch 20%, two tables
+    // 40% each); fewer CTAs when the budget would make slices too small
+    const uint64_t align = 256, min_table = 1ull << 20;
+    const uint64_t result_bytes = ws ? ws->result_bytes : (budget * 2 / 5) / align * align;
+    const uint64_t slices_bytes = ws ? ws->arena_bytes : budget - result_bytes;
+    int grid = nsm * per_sm;
+    while (grid > 1 && (slices_bytes / (uint64_t)grid) * 2 / 5 < min_table) grid /= 2;
+    const uint64_t slice = (slices_bytes / (uint64_t)grid) / align * align;
+    const uint64_t s_bytes = (slice / 5) / align * align;
+    const uint64_t t_bytes = ((slice - s_bytes) / 2) / align * align;
+    if (t_bytes < min_table) {
+        for (BatchPlan &p : plans)                        // too small for any slice: all on the plain path
+            if (p.active) p.failed = true;
+        return GSI_OK;
+    }
+    // seed words per item: at most one table region of seeds
+    const uint64_t max_words = std::max<uint64_t>(1, (t_bytes - 1024) / 128);
+    for (int i = 0; i < nq; ++i) {
+        BatchPlan &p = plans[i];
+        std::memset(&bqs[i], 0, sizeof(BatchQuery));
+        bqs[i].k = p.k;
+        bqs[i].count_only = o.count_only;
+        if (!p.active) continue;
+        bqs[i].seed_bm = p.bitmaps + (uint64_t)p.order[0] * (uint64_t)g->nwords;
+        for (int t = 1; t < p.k; ++t) {
+            const int co = (t == p.k - 1) && o.count_only;
+            cfg[(size_t)i * GSI_MAX_QUERY_VERTICES + t] =
+                make_join_args(g, p.steps[t], p.bitmaps + (uint64_t)p.order[t] * (uint64_t)g->nwords, co, dstats);
+        }
+        // split the seed bitmap into word ranges holding about seeds_per_item
+        // seeds each (and never more words than a table region can take)
+        const uint64_t nw = (uint64_t)g->nwords;
+        const uint64_t per = o.seeds_per_item > 0 ? (uint64_t)o.seeds_per_item : 32;
+        uint64_t parts = std::max<uint64_t>((p.seed_count + per - 1) / per, (nw + max_words - 1) / max_words);
+        if (parts < 1) parts = 1;
+        if (parts > nw) parts = nw;
+        for (uint64_t j = 0; j < parts; ++j) {
+            BatchItem it;
+            it.q = i;
+            it.pad = 0;
+            it.word_lo = (int64_t)(nw * j / parts);
+            it.word_hi = (int64_t)(nw * (j + 1) / parts);
+            if (it.word_hi > it.word_lo) items.push_back(it);
+        }
     }
     const size_t ctl_bytes = sizeof(JoinArgs) * cfg.size() + sizeof(BatchQuery) * bqs.size() +
                              sizeof(BatchItem) * items.size() + sizeof(BatchRec) * items.size() + 64;
@@ -258,9 +276,20 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
         if (arena) cudaFreeAsync(arena, st);
         if (result) cudaFreeAsync(result, st);
     };
+    auto free_all_ws = [&]() {
+        if (ctl) cudaFreeAsync(ctl, st);
+    };
+    if (ws) {
+        arena = ws->arena;
+        result = ws->result;
+    }
     if (cudaMallocAsync(&ctl, ctl_bytes, st) != cudaSuccess ||
-        cudaMallocAsync(&arena, slice * (uint64_t)grid, st) != cudaSuccess ||
-        cudaMallocAsync(&result, result_bytes, st) != cudaSuccess) {
+        (!ws && cudaMallocAsync(&arena, slice * (uint64_t)grid, st) != cudaSuccess) ||
+        (!ws && cudaMallocAsync(&result, result_bytes, st) != cudaSuccess)) {
+        if (ws) {
+            arena = nullptr;
+            result = nullptr;
+        }
         free_all();
         (void)cudaGetLastError();
         set_error("batch: could not reserve the batch arena");
@@ -306,6 +335,7 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
         ba.slice_bytes = slice;
         ba.s_bytes = s_bytes;
         ba.t_bytes = t_bytes;
+        ba.item_rows = o.item_rows > 0 ? (uint64_t)o.item_rows : 0;
         k_batch<<<grid, BNT, sm, st>>>(ba);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("batch: kernel launch failed");
@@ -343,7 +373,35 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
     }
     if (dstats) cudaFreeAsync(dstats, st);
     if (rc != GSI_OK) {
-        free_all();
+        if (ws) free_all_ws();
+        else free_all();
+        return rc;
+    }
+    if (ws) {
+        // copy each query's rows out of the reusable staging area
+        for (int i = 0; i < nq; ++i) {
+            BatchPlan &p = plans[i];
+            if (!p.active) continue;
+            p.failed = bqs[i].status != 0;
+            p.count = bqs[i].count;
+        }
+        for (size_t j = 0; j < items.size() && rc == GSI_OK; ++j) {
+            const int qi = items[j].q;
+            if (bqs[qi].status || !recs[j].rows) continue;
+            const uint64_t bytes = recs[j].rows * (uint64_t)plans[qi].k * 4;
+            int32_t *own = nullptr;
+            if (cudaMallocAsync(&own, bytes, st) != cudaSuccess ||
+                cudaMemcpyAsync(own, result + recs[j].off, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                set_error("batch: result copy failed");
+                rc = GSI_ENOMEM;
+                if (own) cudaFreeAsync(own, st);
+                break;
+            }
+            gsi_result::Chunk ch{own, recs[j].rows, true};
+            plans[qi].chunks.push_back(ch);
+        }
+        if (rc == GSI_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GSI_ECUDA;
+        free_all_ws();
         return rc;
     }
     // results: chunks point into the shared result arena, which the last
@@ -351,6 +409,8 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
     auto shared = std::make_shared<ResultArena>();
     shared->ptr = result;
     shared->device = g->device;
+    shared->stream = st;
+    shared->own_stream = true;
     result = nullptr;
     for (size_t j = 0; j < items.size(); ++j) {
         const int qi = items[j].q;

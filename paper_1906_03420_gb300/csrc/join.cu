@@ -150,7 +150,7 @@ __device__ __forceinline__ void cta_prefix(const unsigned long long *bsum, unsig
                                            unsigned long long *pre, unsigned long long *tot) {
     unsigned long long p = 0, q = 0;
     for (unsigned j = threadIdx.x; j < nblocks; j += blockDim.x) {
-        const unsigned long long v = bsum[j];
+        const unsigned long long v = __ldcg(bsum + j);
         q += v;
         if (j < blockIdx.x) p += v;
     }
@@ -201,9 +201,9 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
     for (int t = 1; t < k; ++t) {
         DStep *st = steps + t;
         const JoinArgs &a = cfgs[t];
-        const uint64_t R = steps[t - 1].count;
+        const uint64_t R = __ldcg(&steps[t - 1].count);
         // the previous table must have fit its region; the scratch must fit too
-        if (t > 1 && steps[t - 1].count > steps[t - 1].out_cap) {
+        if (t > 1 && R > __ldcg(&steps[t - 1].out_cap)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 2u);
             return;
         }
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             int64_t l2 = 0, h2 = (int64_t)R;
             while (l2 < h2) {
                 int64_t mid = (l2 + h2 + 1) >> 1;
-                if (F[mid] <= sl) l2 = mid;
+                if (__ldcg(F + mid) <= sl) l2 = mid;
                 else h2 = mid - 1;
             }
             part[b] = l2;
@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             __syncthreads();
             const uint64_t tile = tile_s;
             if (tile >= ntiles) break;
-            join_tile<NT, VT>(a, M, (int64_t)R, F, total, part[tile], part[tile + 1], st->out, cap, &st->count, tile);
+            join_tile<NT, VT>(a, M, (int64_t)R, F, total, __ldcg(part + tile), __ldcg(part + tile + 1), st->out, cap,
+                              &st->count, tile);
         }
         if (!grid_barrier(ctl, G)) return;
     }

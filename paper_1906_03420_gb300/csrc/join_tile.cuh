@@ -34,11 +34,14 @@ struct StepDev {
 };
 
 // Row i's output bound: the shortest label sub-list over its linking edges.
-__device__ inline uint32_t row_bound(const StepDev &s, const int32_t *__restrict__ row, const uint32_t *__restrict__ off,
+// `row` may have been written earlier in the same launch by other CTAs (the
+// one-launch-per-query and batched kernels reuse their table regions), so it
+// is read through L2 (ld.global.cg), never through the read-only path.
+__device__ inline uint32_t row_bound(const StepDev &s, const int32_t *row, const uint32_t *__restrict__ off,
                                      const uint16_t *__restrict__ cl) {
     uint32_t best = 0xffffffffu;
     for (int j = 0; j < s.d; ++j) {
-        uint64_t seg = (uint64_t)(uint32_t)row[s.col[j]] * (uint64_t)s.L + (uint64_t)s.lab[j];
+        uint64_t seg = (uint64_t)(uint32_t)__ldcg(row + s.col[j]) * (uint64_t)s.L + (uint64_t)s.lab[j];
         uint32_t a = __ldg(off + seg), b = __ldg(off + seg + 1), lo, hi;
         label_range(cl, a, b, (uint32_t)s.ulab, &lo, &hi);
         best = min(best, hi - lo);
@@ -95,10 +98,13 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
 // One tile of NV candidate slots.  The table-dependent inputs (M, R, F,
 // total, part, out, out_cap, out_count) are arguments so that the same code
 // serves host-sized launches (one CTA per tile) and device-sized persistent
-// launches (CTAs take tiles from a counter).
+// launches (CTAs take tiles from a counter).  M and F can be rewritten within
+// one persistent launch (ping-pong table regions, one scratch region for
+// every step), so they are read through L2 (ld.global.cg) and never through
+// the non-coherent read-only path.
 template <int NT, int VT>
-__device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *__restrict__ M, int64_t R,
-                                          const uint64_t *__restrict__ F, uint64_t total, int64_t r_lo,
+__device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, int64_t R,
+                                          const uint64_t *F, uint64_t total, int64_t r_lo,
                                           int64_t r_next, int32_t *__restrict__ out, uint64_t out_cap,
                                           unsigned long long *out_count, uint64_t tile) {
     constexpr int NV = NT * VT;
@@ -124,13 +130,13 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *__re
 
     // ---- stage the tile's rows: values, candidate sub-list, other sub-lists
     for (int x = threadIdx.x; x < NV; x += NT) rowmap[x] = 0;
-    for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = F[r_lo + lr];
+    for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = __ldcg(F + r_lo + lr);
     __syncthreads();
     unsigned long long bytes = 0;
     for (int lr = threadIdx.x; lr < nr; lr += NT) {
         const int32_t *row = M + (r_lo + lr) * (int64_t)t;
         int32_t *rv = rowv + lr * t;
-        for (int c = 0; c < t; ++c) rv[c] = row[c];
+        for (int c = 0; c < t; ++c) rv[c] = __ldcg(row + c);
         // the row's lists: the shortest label sub-list supplies candidates
         uint32_t lo[GSI_MAX_QUERY_VERTICES], len[GSI_MAX_QUERY_VERTICES];
         uint32_t best = 0xffffffffu;

@@ -229,6 +229,11 @@ void Timer::resolve(gsi_stats *s) {
 }
 
 // ----------------------------------------------------------------- driver
+// First device-driven arena of a query.  Reserving an arena near the whole
+// default budget (a large share of HBM) from the stream-ordered pool costs
+// milliseconds per query; arenas up to tens of GB cost well under one.
+constexpr uint64_t DEVICE_ARENA_START = 8ull << 30;
+
 static gsi_status dalloc(Exec &x, void **p, uint64_t bytes) {
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, x.st);
     if (e != cudaSuccess) {
@@ -368,14 +373,16 @@ gsi_status Exec::run(int t, const int32_t *M, uint64_t R) {
 // region and two table regions used in turn), every step's sizes computed on
 // the device, no host wait until the end.  The final table's region is handed
 // to the result when it is well used, or its rows are copied to a tight buffer.
-gsi_status Exec::run_device(bool *overflow) {
+gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memory) {
     *overflow = false;
-    const uint64_t B = budget;
+    *no_memory = false;
+    const uint64_t B = arena_bytes;
     const uint64_t align = 256;
     const uint64_t s_bytes = (B / 5) / align * align;
     const uint64_t t_bytes = ((B - s_bytes) / 2) / align * align;
     if (s_bytes < (1 << 16) || t_bytes < (uint64_t)g->n * 4 + 1024) {
         *overflow = true;
+        *no_memory = true;
         return GSI_OK;
     }
     uint64_t *S = nullptr;
@@ -397,6 +404,7 @@ gsi_status Exec::run_device(bool *overflow) {
         release();
         (void)cudaGetLastError();
         *overflow = true;              // could not reserve the arena: use the splitting path
+        *no_memory = true;
         return GSI_OK;
     }
     peak = std::max(peak, s_bytes + 2 * t_bytes);
@@ -509,6 +517,8 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     std::unique_ptr<gsi_result> res(new gsi_result());
     res->k = q.k;
     res->device = g->device;
+    res->stream = (cudaStream_t)o.stream;
+    res->own_stream = true;
     Exec x;
     x.g = g;
     x.k = q.k;
@@ -618,7 +628,16 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         make_steps(q, order, first, ranks, x.steps);
         // device-driven path first; the host-driven splitting path on overflow
         bool overflow = true;
-        if (!o.host_driven && q.k > 1) rc = x.run_device(&overflow);
+        if (!o.host_driven && q.k > 1) {
+            // arenas of 8 GiB, then x4 per overflow, up to the budget
+            uint64_t arena = std::min<uint64_t>(x.budget, DEVICE_ARENA_START);
+            for (;;) {
+                bool no_memory = false;
+                rc = x.run_device(arena, &overflow, &no_memory);
+                if (rc != GSI_OK || !overflow || no_memory || arena >= x.budget) break;
+                arena = std::min<uint64_t>(x.budget, arena * 4);
+            }
+        }
         x.fell_back = overflow;
         const uint64_t R0 = cand_h[order[0]];
         int32_t *M0 = nullptr;

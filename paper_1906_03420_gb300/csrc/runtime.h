@@ -15,6 +15,8 @@ namespace gsi {
 struct ResultArena {
     int32_t *ptr = nullptr;
     int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
     ~ResultArena();
 };
 }  // namespace gsi
@@ -31,6 +33,11 @@ struct gsi_result {
     uint64_t materialised = 0;   // rows held in chunks
     std::vector<Chunk> chunks;
     std::shared_ptr<gsi::ResultArena> arena;
+    // memory is released stream-ordered on this stream (the one the result was
+    // produced on, so the next query on it reuses the memory at once); null
+    // selects the library's own release stream
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;           // true: `stream` is the producing stream
     ~gsi_result();
 };
 
@@ -79,7 +86,9 @@ struct Exec {
     gsi_status run(int t, const int32_t *M, uint64_t R);
     // All steps enqueued with device-resident sizes; *overflow is set when a
     // table or the scratch did not fit its region (nothing is added to res).
-    gsi_status run_device(bool *overflow);
+    // arena_bytes: scratch + two table regions; *overflow: a table did not
+    // fit (or the arena could not be reserved: *no_memory as well)
+    gsi_status run_device(uint64_t arena_bytes, bool *overflow, bool *no_memory);
     gsi_status add_chunk(int32_t *rows, uint64_t nrows, uint64_t alloc_rows);
     const uint32_t *cand(const JoinStep &s, int t) const;
 };
@@ -101,10 +110,21 @@ struct BatchPlan {
 };
 
 gsi_status plan_for_batch(gsi_graph *g, BatchPlan &p, const uint64_t *cand_counts, const int32_t *ranks);
+// Device memory a server slot keeps across batches (allocated once): the
+// per-CTA slices and the result staging area.  Results of a batch run with a
+// workspace are copied into their own buffers, so the workspace is reusable.
+struct BatchWorkspace {
+    unsigned char *arena = nullptr;
+    uint64_t arena_bytes = 0;
+    int32_t *result = nullptr;
+    uint64_t result_bytes = 0;
+};
+
 gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
-                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses);
+                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses,
+                         BatchWorkspace *ws = nullptr);
 gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o, uint64_t budget,
-                            cudaStream_t st, gsi_stats *stats);
+                            cudaStream_t st, gsi_stats *stats, BatchWorkspace *ws = nullptr);
 gsi_status prepare_device(int dev);
 gsi_status validate_query(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
                           const int32_t *qelab, int32_t qm, QueryGraph *q);

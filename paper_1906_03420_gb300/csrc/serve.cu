@@ -26,7 +26,7 @@ using namespace gsi;
 // status in plans[i].status.
 namespace gsi {
 gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
-                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses) {
+                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses, BatchWorkspace *ws) {
     const int32_t nq = (int32_t)plans.size();
     outs.assign((size_t)nq, nullptr);
     statuses.assign((size_t)nq, GSI_OK);
@@ -118,7 +118,7 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
         }
         plan_for_batch(g, p, c, ranks.data() + (size_t)i * GSI_MAX_QUERY_VERTICES);
     }
-    if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats);
+    if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats, ws);
     if (bitmaps) cudaFreeAsync(bitmaps, st);
     if (counts) cudaFreeAsync(counts, st);
     if (rc != GSI_OK) return rc;
@@ -140,17 +140,22 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
             gsi_result *r = new gsi_result();
             r->k = p.k;
             r->device = g->device;
+            r->stream = st;
+            r->own_stream = true;
             r->count = p.active ? p.count : 0;
             uint64_t keep = bo.count_only ? 0 : (bo.row_cap ? bo.row_cap : UINT64_MAX);
             for (auto &c : p.chunks) {
                 if (r->materialised >= keep) break;
                 gsi_result::Chunk ch = c;
                 ch.nrows = std::min<uint64_t>(ch.nrows, keep - r->materialised);
-                ch.owned = false;
+                if (!ws) ch.owned = false;       // rows live in the batch's shared arena
                 r->chunks.push_back(ch);
                 r->materialised += ch.nrows;
             }
             r->arena = p.arena;
+            // owned chunks beyond the row cap are released here
+            if (ws)
+                for (size_t ci = r->chunks.size(); ci < p.chunks.size(); ++ci) cudaFreeAsync(p.chunks[ci].rows, st);
             outs[i] = r;
         }
         statuses[i] = qrc;
@@ -188,6 +193,57 @@ extern "C" gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int3
     }
 }
 
+extern "C" gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs, int32_t nq,
+                                         const gsi_batch_opts *opts, int32_t *best_seeds_per_item, double *best_ms) {
+    if (!g || nq < 1 || !qs) {
+        set_error("gsi_batch_autotune: need a graph and at least one query");
+        return GSI_EINVAL;
+    }
+    try {
+        gsi_batch_opts bo;
+        std::memset(&bo, 0, sizeof bo);
+        if (opts) bo = *opts;
+        bo.stats = nullptr;
+        std::vector<BatchPlan> proto((size_t)nq);
+        for (int32_t i = 0; i < nq; ++i)
+            proto[i].status = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm,
+                                             &proto[i].q);
+        const int32_t cand[] = {16, 32, 64, 128, 256};
+        double best = 1e300;
+        int32_t arg = 32;
+        for (int32_t c : cand) {
+            double t_best = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                std::vector<BatchPlan> plans((size_t)nq);
+                for (int32_t i = 0; i < nq; ++i) {
+                    plans[i].status = proto[i].status;
+                    plans[i].q = proto[i].q;
+                }
+                bo.seeds_per_item = c;
+                std::vector<gsi_result *> res;
+                std::vector<gsi_status> sts;
+                auto t0 = std::chrono::steady_clock::now();
+                gsi_status rc = batch_execute(g, plans, bo, res, sts);
+                if (bo.stream) cudaStreamSynchronize((cudaStream_t)bo.stream);
+                auto t1 = std::chrono::steady_clock::now();
+                for (gsi_result *r : res) delete r;
+                if (rc != GSI_OK) return rc;
+                t_best = std::min(t_best, std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            if (t_best < best) {
+                best = t_best;
+                arg = c;
+            }
+        }
+        if (best_seeds_per_item) *best_seeds_per_item = arg;
+        if (best_ms) *best_ms = best;
+        return GSI_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("gsi_batch_autotune: host allocation failed");
+        return GSI_ENOMEM;
+    }
+}
+
 // ------------------------------------------------------------------ server
 struct gsi_server {
     gsi_graph *g = nullptr;
@@ -215,13 +271,32 @@ struct gsi_server {
 // memory budget.  It takes every pending request (up to max_batch) as one
 // batch, so requests that arrived while other batches were on the GPU are
 // admitted as soon as a slot frees; batches of different slots overlap on
-// the device.  With max_batch == 1 a slot runs one query at a time on the
-// plain path.
+// the device.  With max_batch == 1, or fewer than min_batch requests pending,
+// a slot runs one query at a time on the plain path.
 static void server_worker(gsi_server *s, int idx) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = s->streams[idx];
     const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
     const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
+    const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 8;
+    // the slot's batch workspace, allocated once (results are copied out)
+    BatchWorkspace ws;
+    if (max_batch > 1) {
+        ws.result_bytes = (share / 5) / 256 * 256;
+        ws.arena_bytes = (share - ws.result_bytes) / 256 * 256;
+        if (cudaMalloc(&ws.arena, ws.arena_bytes) != cudaSuccess || cudaMalloc(&ws.result, ws.result_bytes) != cudaSuccess) {
+            if (ws.arena) cudaFree(ws.arena);
+            ws = BatchWorkspace();
+            (void)cudaGetLastError();
+        }
+    }
+    struct WsGuard {
+        BatchWorkspace &w;
+        ~WsGuard() {
+            if (w.arena) cudaFree(w.arena);
+            if (w.result) cudaFree(w.result);
+        }
+    } wsg{ws};
     for (;;) {
         std::vector<std::shared_ptr<gsi_server::Req>> batch;
         {
@@ -244,38 +319,53 @@ static void server_worker(gsi_server *s, int idx) {
         }
         std::vector<gsi_result *> res(batch.size(), nullptr);
         std::vector<gsi_status> sts(batch.size(), GSI_OK);
-        if (batch.size() == 1 && max_batch == 1) {
-            gsi_query_opts o;
-            std::memset(&o, 0, sizeof o);
-            o.stream = st;
-            o.row_cap = s->opts.row_cap;
-            o.count_only = s->opts.count_only;
-            o.mem_budget = share;
-            sts[0] = run_query(s->g, batch[0]->q, o, &res[0]);
-        } else {
-            std::vector<BatchPlan> plans(batch.size());
-            for (size_t i = 0; i < batch.size(); ++i) plans[i].q = batch[i]->q;
-            gsi_batch_opts bo;
-            std::memset(&bo, 0, sizeof bo);
-            bo.stream = st;
-            bo.row_cap = s->opts.row_cap;
-            bo.mem_budget = share;
-            bo.count_only = s->opts.count_only;
-            gsi_status rc = batch_execute(s->g, plans, bo, res, sts);
-            if (rc != GSI_OK)
-                for (size_t i = 0; i < batch.size(); ++i)
-                    if (sts[i] == GSI_OK && !res[i]) sts[i] = rc;
-        }
-        auto now = std::chrono::steady_clock::now();
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (size_t i = 0; i < batch.size(); ++i) {
-                batch[i]->res = res[i];
-                batch[i]->status = sts[i];
-                batch[i]->latency_ms = std::chrono::duration<double, std::milli>(now - batch[i]->t_submit).count();
+        // hand results [lo, hi) to their requests
+        auto publish = [&](size_t lo, size_t hi) {
+            auto now = std::chrono::steady_clock::now();
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (size_t i = lo; i < hi; ++i) {
+                    if (res[i]) {                  // slot streams are the server's: release elsewhere
+                        res[i]->own_stream = false;
+                        if (res[i]->arena) res[i]->arena->own_stream = false;
+                    }
+                    batch[i]->res = res[i];
+                    batch[i]->status = sts[i];
+                    batch[i]->latency_ms = std::chrono::duration<double, std::milli>(now - batch[i]->t_submit).count();
+                }
             }
+            s->cv_done.notify_all();
+        };
+        if (max_batch == 1 || batch.size() < min_batch) {
+            // too few requests to fill the GPU with (query, seed range) items:
+            // one query at a time on the plain path, every step on all SMs
+            for (size_t i = 0; i < batch.size(); ++i) {
+                gsi_query_opts o;
+                std::memset(&o, 0, sizeof o);
+                o.stream = st;
+                o.row_cap = s->opts.row_cap;
+                o.count_only = s->opts.count_only;
+                o.mem_budget = share;
+                sts[i] = run_query(s->g, batch[i]->q, o, &res[i]);
+                publish(i, i + 1);
+            }
+            continue;
         }
-        s->cv_done.notify_all();
+        std::vector<BatchPlan> plans(batch.size());
+        for (size_t i = 0; i < batch.size(); ++i) plans[i].q = batch[i]->q;
+        gsi_batch_opts bo;
+        std::memset(&bo, 0, sizeof bo);
+        bo.stream = st;
+        bo.row_cap = s->opts.row_cap;
+        bo.mem_budget = share;
+        bo.count_only = s->opts.count_only;
+        bo.seeds_per_item = s->opts.seeds_per_item;
+        bo.item_rows = s->opts.item_rows;
+        gsi_status rc = batch_execute(s->g, plans, bo, res, sts, ws.arena ? &ws : nullptr);
+        if (rc != GSI_OK)
+            for (size_t i = 0; i < batch.size(); ++i)
+                if (sts[i] == GSI_OK && !res[i]) sts[i] = rc;
+        publish(0, batch.size());
     }
 }
 

@@ -26,7 +26,7 @@ EXPORTED = [
     "gsi_graph_create", "gsi_graph_destroy", "gsi_graph_get_info", "gsi_graph_export", "gsi_graph_label_freq",
     "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_destroy",
     "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_join_step_noalloc", "gsi_plan_order",
-    "gsi_batch_run", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
+    "gsi_batch_run", "gsi_batch_autotune", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
     "gsi_server_destroy", "gsi_last_error", "gsi_version", "gsi_selftest_wait_timeout",
 ]
 
@@ -78,12 +78,14 @@ class c_query_desc(ctypes.Structure):
 
 class c_batch_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
-                ("count_only", ctypes.c_int32), ("stats", ctypes.POINTER(c_stats))]
+                ("count_only", ctypes.c_int32), ("stats", ctypes.POINTER(c_stats)),
+                ("seeds_per_item", ctypes.c_int32), ("item_rows", ctypes.c_int32)]
 
 
 class c_server_opts(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_uint64), ("n_streams", ctypes.c_int32), ("row_cap", ctypes.c_uint64),
-                ("count_only", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+                ("count_only", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("seeds_per_item", ctypes.c_int32),
+                ("item_rows", ctypes.c_int32), ("min_batch", ctypes.c_int32)]
 
 
 _lib = None
@@ -147,6 +149,9 @@ def load(build_if_missing: bool = False):
     L.gsi_batch_run.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
                                 ctypes.POINTER(VP), I32P]
     L.gsi_batch_run.restype = st
+    L.gsi_batch_autotune.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
+                                     I32P, ctypes.POINTER(ctypes.c_double)]
+    L.gsi_batch_autotune.restype = st
     L.gsi_server_create.argtypes = [VP, ctypes.POINTER(c_server_opts), ctypes.POINTER(VP)]
     L.gsi_server_create.restype = st
     L.gsi_server_submit.argtypes = [VP, ctypes.POINTER(c_query_desc), U64P]
@@ -363,18 +368,30 @@ class Graph:
         return int(cnt.value)
 
     def batch(self, queries, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
-              stats: c_stats | None = None) -> list:
+              stats: c_stats | None = None, seeds_per_item: int = 0, item_rows: int = 0) -> list:
         qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
         descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
         outs = (VP * len(qas))()
         sts = (ctypes.c_int32 * len(qas))()
         o = c_batch_opts(_stream_handle(stream), row_cap, mem_budget, int(count_only),
-                         ctypes.pointer(stats) if stats is not None else None)
+                         ctypes.pointer(stats) if stats is not None else None, seeds_per_item, item_rows)
         _check(load().gsi_batch_run(self._h, descs, len(qas), ctypes.byref(o), outs, sts), "gsi_batch_run")
         res = []
         for i in range(len(qas)):
             res.append(Result(outs[i]) if sts[i] == GSI_OK else GsiError(sts[i], "batched query failed"))
         return res
+
+
+def batch_autotune(graph: "Graph", queries, stream=None, mem_budget: int = 0) -> tuple[int, float]:
+    """Pick the batch work-item size on a calibration batch: (seeds_per_item, ms)."""
+    qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
+    descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
+    o = c_batch_opts(_stream_handle(stream), 0, mem_budget, 0, None, 0, 0)
+    best = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(load().gsi_batch_autotune(graph.handle, descs, len(qas), ctypes.byref(o), ctypes.byref(best),
+                                     ctypes.byref(ms)), "gsi_batch_autotune")
+    return int(best.value), float(ms.value)
 
 
 def query_signatures(q) -> np.ndarray:
@@ -401,10 +418,12 @@ class Server:
     """Continuous-batching server over a resident graph (gsi_server_*)."""
 
     def __init__(self, graph: Graph, mem_budget: int = 0, n_streams: int = 2, row_cap: int = 0,
-                 count_only: bool = False, max_batch: int = 0):
+                 count_only: bool = False, max_batch: int = 0, seeds_per_item: int = 0, item_rows: int = 0,
+                 min_batch: int = 0):
         self._graph = graph
         h = VP()
-        o = c_server_opts(mem_budget, n_streams, row_cap, int(count_only), max_batch)
+        o = c_server_opts(mem_budget, n_streams, row_cap, int(count_only), max_batch, seeds_per_item, item_rows,
+                          min_batch)
         _check(load().gsi_server_create(graph.handle, ctypes.byref(o), ctypes.byref(h)), "gsi_server_create")
         self._h = h.value
 

@@ -97,6 +97,15 @@ def test_batch_small_budget_falls_back(pkg, world):
         assert np.array_equal(oracle.sort_rows(r.rows()), want)
 
 
+def test_batch_tiny_budget_runs_everything_on_the_plain_path(pkg, world):
+    g, G, O, qs = world
+    st = pkg.c_stats()
+    res = G.batch(qs[:6], mem_budget=2 << 20, stats=st)
+    for q, r in zip(qs[:6], res):
+        assert r.count == oracle.count(O, q)[0]
+    assert st.host_driven >= 1
+
+
 def test_batch_results_outlive_each_other(pkg, world):
     """Results of one batch share an arena; destroying some keeps the others valid."""
     g, G, O, qs = world
@@ -108,3 +117,19 @@ def test_batch_results_outlive_each_other(pkg, world):
             r.close()
     del res
     assert np.array_equal(oracle.sort_rows(keep.rows()), want)
+
+
+def test_batch_autotune_and_item_sizes(pkg, world):
+    """The autotuner returns one of its candidate sizes; every item size gives the same results."""
+    g, G, O, qs = world
+    best, ms = pkg.batch_autotune(G, qs[:16])
+    assert best in (16, 32, 64, 128, 256) and ms > 0
+    ref = [oracle.count(O, q)[0] for q in qs[:16]]
+    for spi in (1, 7, 32, 4096):
+        res = G.batch(qs[:16], seeds_per_item=spi)
+        assert [r.count for r in res] == ref
+    # a small item table limit sends the larger queries to the plain path, same results
+    st = pkg.c_stats()
+    res = G.batch(qs[:16], item_rows=64, stats=st)
+    assert [r.count for r in res] == ref
+    assert st.host_driven >= 1

@@ -41,11 +41,12 @@ def _serve_all(S, qs):
     return out
 
 
-@pytest.mark.parametrize("n_streams,max_batch", [(2, 0), (3, 4), (1, 1)])
-def test_served_result_equals_alone(pkg, world, n_streams, max_batch):
-    """Each query's result is the same alone (plain path) and served in the mix."""
+@pytest.mark.parametrize("n_streams,max_batch,min_batch", [(2, 0, 1), (3, 4, 2), (1, 1, 0), (2, 0, 0), (1, 0, 16)])
+def test_served_result_equals_alone(pkg, world, n_streams, max_batch, min_batch):
+    """Each query's result is the same alone (plain path) and served in the mix,
+    whether the slots batch, run one at a time, or switch by queue length."""
     g, G, qs = world
-    S = pkg.Server(G, mem_budget=8 << 30, n_streams=n_streams, max_batch=max_batch)
+    S = pkg.Server(G, mem_budget=8 << 30, n_streams=n_streams, max_batch=max_batch, min_batch=min_batch)
     served = _serve_all(S, qs)
     for q, (r, lat) in zip(qs, served):
         alone = G.query(q)
@@ -83,3 +84,16 @@ def test_bounded_device_wait_runs_out(pkg):
     assert ms < 5000
     x = torch.arange(1000, device="cuda").sum().item()   # the context still works
     assert x == 499500
+
+
+def test_served_workspace_reuse(pkg, world):
+    """A slot's batch workspace is reused by batches of changing composition;
+    every batch must see only its own data (a missing barrier between the
+    seed writes and the first join step once let stale seeds through)."""
+    g, G, qs = world
+    alone = [G.query(q).count for q in qs]
+    for _ in range(20):
+        S = pkg.Server(G, mem_budget=8 << 30, n_streams=1, max_batch=0, min_batch=1)
+        served = _serve_all(S, qs)
+        S.close()
+        assert [r.count for r, _ in served] == alone
