@@ -259,15 +259,25 @@ typedef struct {
     gsi_stats *stats;        /* optional, accumulated over the batch */
     int32_t seeds_per_item;  /* work-item size: candidates of the first query
                                 vertex per (query, range) item; 0 = 32 */
-    int32_t item_rows;       /* a query whose item's table grows past this many
-                                rows leaves the batch and runs on the plain path
-                                (all SMs); 0 = only when the table does not fit */
+    int32_t item_rows;       /* split size: a work unit whose table has more
+                                rows than this after a step keeps this many and
+                                queues the rest, in pieces of this many rows,
+                                for other CTAs; 0 = 4096, < 0 = never split */
 } gsi_batch_opts;
 
 /*
- * Run nq queries together (a shared work queue of (query, step, row-range)
- * tiles).  outs[i] receives query i's result (or NULL if its status is not
- * GSI_OK); statuses (optional, int32[nq]) receives per-query status.
+ * Run nq queries together in one persistent launch (no counterpart in the
+ * paper, which runs one query at a time): one filter pass over every query
+ * vertex of the batch (Sec. III-A), the Alg. 2 order per query, then work
+ * units on shared queues.  A seed unit is a range of one query's first
+ * candidate set; a CTA runs every join step (Alg. 3, Alg. 4 bound) on its
+ * rows in its own memory slice, and rows past item_rows after a step go back
+ * to a queue as new units, so large queries spread over the GPU.  Queries
+ * whose tables do not fit a slice (or the batch result area) run again on
+ * the plain path of gsi_query_run.  The rows of each result are those
+ * gsi_query_run returns, in another order.  outs[i] receives query i's
+ * result (or NULL if its status is not GSI_OK); statuses (optional,
+ * int32[nq]) receives per-query status.
  */
 gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
                          gsi_result **outs, int32_t *statuses);

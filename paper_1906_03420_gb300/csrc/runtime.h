@@ -112,7 +112,8 @@ struct BatchPlan {
 gsi_status plan_for_batch(gsi_graph *g, BatchPlan &p, const uint64_t *cand_counts, const int32_t *ranks);
 // Device memory a server slot keeps across batches (allocated once): the
 // per-CTA slices and the result staging area.  Results of a batch run with a
-// workspace are copied into their own buffers, so the workspace is reusable.
+// workspace are gathered into one tight buffer that the batch's results
+// share, so the workspace is reusable at once.
 struct BatchWorkspace {
     unsigned char *arena = nullptr;
     uint64_t arena_bytes = 0;

@@ -148,14 +148,11 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
                 if (r->materialised >= keep) break;
                 gsi_result::Chunk ch = c;
                 ch.nrows = std::min<uint64_t>(ch.nrows, keep - r->materialised);
-                if (!ws) ch.owned = false;       // rows live in the batch's shared arena
+                ch.owned = false;                // rows live in the batch's shared buffer
                 r->chunks.push_back(ch);
                 r->materialised += ch.nrows;
             }
             r->arena = p.arena;
-            // owned chunks beyond the row cap are released here
-            if (ws)
-                for (size_t ci = r->chunks.size(); ci < p.chunks.size(); ++ci) cudaFreeAsync(p.chunks[ci].rows, st);
             outs[i] = r;
         }
         statuses[i] = qrc;
@@ -279,7 +276,7 @@ static void server_worker(gsi_server *s, int idx) {
     const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
     const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
     const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 8;
-    // the slot's batch workspace, allocated once (results are copied out)
+    // the slot's batch workspace, allocated once (results are gathered out)
     BatchWorkspace ws;
     if (max_batch > 1) {
         ws.result_bytes = (share / 5) / 256 * 256;

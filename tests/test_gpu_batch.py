@@ -128,8 +128,14 @@ def test_batch_autotune_and_item_sizes(pkg, world):
     for spi in (1, 7, 32, 4096):
         res = G.batch(qs[:16], seeds_per_item=spi)
         assert [r.count for r in res] == ref
-    # a small item table limit sends the larger queries to the plain path, same results
-    st = pkg.c_stats()
-    res = G.batch(qs[:16], item_rows=64, stats=st)
-    assert [r.count for r in res] == ref
-    assert st.host_driven >= 1
+    # splitting: units that grow past item_rows rows hand pieces to other
+    # CTAs; the results are the same with tiny, default and no splitting
+    units = {}
+    for ir in (-1, 0, 64, 7):
+        st = pkg.c_stats()
+        res = G.batch(qs[:16], item_rows=ir, stats=st)
+        assert [r.count for r in res] == ref
+        for q, r in zip(qs[:4], res[:4]):
+            assert np.array_equal(oracle.sort_rows(r.rows()), oracle.sort_rows(G.query(q).rows()))
+        units[ir] = st.tiles
+    assert units[7] > units[-1] and units[64] > units[-1]

@@ -92,8 +92,8 @@ def test_served_workspace_reuse(pkg, world):
     seed writes and the first join step once let stale seeds through)."""
     g, G, qs = world
     alone = [G.query(q).count for q in qs]
-    for _ in range(20):
-        S = pkg.Server(G, mem_budget=8 << 30, n_streams=1, max_batch=0, min_batch=1)
+    for i in range(20):
+        S = pkg.Server(G, mem_budget=8 << 30, n_streams=1, max_batch=0, min_batch=1, item_rows=16 if i % 2 else 0)
         served = _serve_all(S, qs)
         S.close()
         assert [r.count for r, _ in served] == alone
