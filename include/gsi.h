@@ -262,7 +262,7 @@ typedef struct {
     int32_t item_rows;       /* split size: a work unit whose table has more
                                 rows than this after a step keeps this many and
                                 queues the rest, in pieces of this many rows,
-                                for other CTAs; 0 = 4096, < 0 = never split */
+                                for other CTAs; 0 = 1024, < 0 = never split */
 } gsi_batch_opts;
 
 /*
@@ -284,12 +284,38 @@ gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, con
 
 /*
  * Autotuner for batched execution (no counterpart in the paper): runs the
- * given calibration batch once per candidate work-item size (seeds_per_item
- * in {16, 32, 64, 128, 256}), each twice, and returns the fastest in
- * *best_seeds_per_item with its time in *best_ms (both optional).
+ * given calibration batch once per candidate pair (seeds_per_item in
+ * {32, 64, 128}) x (item_rows in {512, 1024, 2048}), each twice, and returns
+ * the fastest pair in *best_seeds_per_item / *best_item_rows with its time in
+ * *best_ms (all optional).
  */
 gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
-                              int32_t *best_seeds_per_item, double *best_ms);
+                              int32_t *best_seeds_per_item, int32_t *best_item_rows, double *best_ms);
+
+/*
+ * Prepared batches (no counterpart in the paper): the batch of gsi_batch_run
+ * planned once and replayed from a captured CUDA graph.  gsi_batch_prepare
+ * validates the queries (statuses, optional, int32[nq]), runs the batched
+ * filter once to fix each query's Alg. 2 order and join steps, reserves the
+ * batch's device memory (opts->mem_budget, as gsi_batch_run) and captures one
+ * pass of device work (the filter and the batch kernel) into a CUDA graph on
+ * opts->stream (a private stream when NULL: the legacy stream cannot be
+ * captured).  A non-NULL opts->stats only asks the kernels to count
+ * algorithmic bytes on every replay (replays take their own stats).
+ *
+ * gsi_batch_replay launches that graph: every replay recomputes the filter
+ * and all join steps on the device and returns results equal to those of
+ * gsi_batch_run (rows in another order); what it reuses is host work whose
+ * outcome the inputs fix.  outs[i] / statuses[i] as for gsi_batch_run; stats
+ * (optional) accumulates the replay's timings and counters.  Replays of one
+ * prepared batch must not overlap (they share its device memory); results
+ * outlive both later replays and gsi_batch_destroy.
+ */
+typedef struct gsi_batch gsi_batch;
+gsi_status gsi_batch_prepare(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
+                             gsi_batch **out, int32_t *statuses);
+gsi_status gsi_batch_replay(gsi_batch *b, gsi_result **outs, int32_t *statuses, gsi_stats *stats);
+void gsi_batch_destroy(gsi_batch *b);
 
 /* ---------------------------------------------------------------- served */
 typedef struct {
@@ -307,7 +333,7 @@ typedef struct {
     int32_t min_batch;       /* fewer pending requests than this run one at a
                                 time on the plain path (every step on all SMs:
                                 lower latency than a batch too small to fill
-                                the GPU); 0 = 8 */
+                                the GPU); 0 = 16 */
 } gsi_server_opts;
 
 /*

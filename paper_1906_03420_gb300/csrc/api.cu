@@ -81,6 +81,8 @@ gsi_status gsi_graph_create(const int32_t *vlab, int32_t n, const int32_t *src, 
         if (g->ci) cudaFree(g->ci);
         if (g->cl) cudaFree(g->cl);
         if (g->sig) cudaFree(g->sig);
+        if (g->gperm) cudaFree(g->gperm);
+        if (g->gsig) cudaFree(g->gsig);
         return rc;
     }
     *out = g.release();
@@ -98,6 +100,8 @@ void gsi_graph_destroy(gsi_graph *g) {
     cudaFree(g->ci);
     cudaFree(g->cl);
     cudaFree(g->sig);
+    cudaFree(g->gperm);
+    cudaFree(g->gsig);
     if (cur >= 0) cudaSetDevice(cur);
     delete g;
 }

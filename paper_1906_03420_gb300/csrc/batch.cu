@@ -33,7 +33,7 @@ namespace {
 constexpr int BNT = JOIN_NT;
 constexpr int BVT = JOIN_VT;
 constexpr int BNV = BNT * BVT;
-constexpr uint64_t SPILL_SLOTS = 1ull << 16;                  // spill queue capacity (units)
+constexpr uint64_t SPILL_SLOTS = 1ull << 18;                  // spill queue capacity (units)
 constexpr unsigned long long WAIT_SPIN_LIMIT = 1ull << 26;    // x ~100 ns sleeps: several seconds
 constexpr long long UNIT_DONE = -(1ll << 62);
 
@@ -42,7 +42,7 @@ struct BatchQuery {
     int32_t k;
     int32_t count_only;
     unsigned status;               // 1 = failed (table or result arena overflow)
-    unsigned pad;
+    int32_t cfg0;                  // the query's step t uses cfgs[cfg0 + t]
     unsigned long long count;      // embeddings (summed over units)
 };
 
@@ -66,7 +66,9 @@ struct BatchRec {                  // one per unit that kept rows
     unsigned long long rows;
 };
 
-struct BatchCtl {                  // zeroed by the host, except `pending`
+struct BatchCtl {                  // written by the host before every launch
+    int32_t *result;               // result arena
+    unsigned long long result_cap; // int32 elements
     unsigned long long next_item;  // seed queue head
     unsigned long long result_used;
     unsigned long long spill_used; // int32 elements
@@ -79,7 +81,7 @@ struct BatchCtl {                  // zeroed by the host, except `pending`
 };
 
 struct BatchArgs {
-    const JoinArgs *cfgs;          // [q * 32 + t]
+    const JoinArgs *cfgs;          // [cfg0 of the query + t]
     BatchQuery *queries;
     const BatchItem *items;
     int64_t nitems;
@@ -90,8 +92,6 @@ struct BatchArgs {
     int32_t *spill;
     unsigned long long spill_cap;  // int32 elements
     BatchCtl *ctl;
-    int32_t *result;               // result arena
-    unsigned long long result_cap; // int32 elements
     unsigned char *arena;          // per-CTA slices
     uint64_t slice_bytes, s_bytes, t_bytes;
     uint64_t split_rows;           // 0: never split
@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
     const uint64_t S_words = b.s_bytes / 8;
     const uint64_t W = (uint64_t)JOIN_ROW_WEIGHT;
     BatchCtl *c = b.ctl;
+    int32_t *const result = c->result;
+    const unsigned long long result_cap = c->result_cap;
 
     for (;;) {
         if (threadIdx.x == 0) unit_s = next_unit(b);
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
         bool failed = false;
         uint64_t cap = 0;
         for (int t = t0; t < k && R > 0 && !skip; ++t) {
-            const JoinArgs &a = b.cfgs[(size_t)q * GSI_MAX_QUERY_VERTICES + t];
+            const JoinArgs &a = b.cfgs[bq->cfg0 + t];
             int32_t *out = reg[oreg];
             if ((R + 1) * 8 + 64 > S_words * 8) { failed = true; break; }
             uint64_t *F = S;
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
             if (!skip && !failed && rows > 0) {
                 const unsigned long long need = rows * (unsigned long long)k;
                 const unsigned long long o = atomicAdd(&c->result_used, need);
-                if (o + need > b.result_cap) fail_s = 1;
+                if (o + need > result_cap) fail_s = 1;
                 else off_s = o;
             }
             if (fail_s) atomicOr(&bq->status, 1u);
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
         }
         __syncthreads();
         if (!fail_s && rows > 0) {
-            int32_t *dst = b.result + off_s;
+            int32_t *dst = result + off_s;
             const uint64_t n = rows * (uint64_t)k;
             for (uint64_t i = threadIdx.x; i < n; i += BNT) dst[i] = __ldcg(M + i);
         }
@@ -350,22 +352,20 @@ __global__ void __launch_bounds__(256) k_gather(const BatchQuery *__restrict__ q
 
 }  // namespace
 
-// Runs the planned queries of a batch in one k_batch launch; fills each
-// plan's count, failed flag and row chunks.
-gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o,
-                            uint64_t budget, cudaStream_t st, gsi_stats *stats, BatchWorkspace *ws) {
+
+// ------------------------------------------------------------------- host
+// Sizes the launch, lists the seed units, builds the per-step configurations
+// and reserves the control block (and the work area unless a workspace brings
+// one).  With keep_template the initial query records also stay on the device
+// so that replays can reset them with a device copy.
+gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o,
+                       uint64_t budget, cudaStream_t st, BatchWorkspace *ws, bool stats, bool keep_template) {
+    L = BatchLaunch();
     const int nq = (int)plans.size();
-    if (nq == 0) return GSI_OK;
-    // device counters of algorithmic bytes and candidates (only with stats)
-    unsigned long long *dstats = nullptr;
+    L.nq = (size_t)nq;
     if (stats) {
-        GSI_CUDA_TRY(cudaMallocAsync(&dstats, 16, st));
-        GSI_CUDA_TRY(cudaMemsetAsync(dstats, 0, 16, st));
+        GSI_CUDA_TRY(cudaMallocAsync(&L.dstats, 16, st));
     }
-    // configs, queries, items
-    std::vector<JoinArgs> cfg((size_t)nq * GSI_MAX_QUERY_VERTICES);
-    std::vector<BatchQuery> bqs((size_t)nq);
-    std::vector<BatchItem> items;
     size_t sm = join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, 1, 1);
     for (int i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
@@ -374,17 +374,16 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
             sm = std::max(sm, join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, p.steps[t].t, p.steps[t].d));
     }
     if (sm > 200 * 1024) {
-        if (dstats) cudaFreeAsync(dstats, st);
         set_error("batch: shared memory need exceeds 200 KB");
         return GSI_EINVAL;
     }
-    int dev = 0, nsm = 152, per_sm = 0;
+    L.sm = sm;
+    int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
     GSI_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BNT, sm));
     if (per_sm < 1) {
-        if (dstats) cudaFreeAsync(dstats, st);
         set_error("batch: kernel does not fit on an SM");
         return GSI_EINVAL;
     }
@@ -393,24 +392,26 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
     // quarters per-CTA slices (scratch 20%, two tables 40% each), with fewer
     // CTAs when the slices would be too small
     const uint64_t align = 256, min_table = 1ull << 20;
-    const uint64_t result_bytes = ws ? ws->result_bytes : (budget * 3 / 10) / align * align;
-    const uint64_t work_bytes = ws ? ws->arena_bytes : (budget - result_bytes) / align * align;
-    const uint64_t split_rows = o.item_rows < 0 ? 0 : (o.item_rows > 0 ? (uint64_t)o.item_rows : 4096);
-    const uint64_t spill_bytes = split_rows ? (work_bytes / 4) / align * align : 0;
-    const uint64_t slices_bytes = work_bytes - spill_bytes;
-    int grid = nsm * per_sm;
-    while (grid > 1 && (slices_bytes / (uint64_t)grid) * 2 / 5 < min_table) grid /= 2;
-    const uint64_t slice = (slices_bytes / (uint64_t)grid) / align * align;
-    const uint64_t s_bytes = (slice / 5) / align * align;
-    const uint64_t t_bytes = ((slice - s_bytes) / 2) / align * align;
-    if (t_bytes < min_table) {
-        for (BatchPlan &p : plans)                        // too small for any slice: all on the plain path
-            if (p.active) p.failed = true;
-        if (dstats) cudaFreeAsync(dstats, st);
+    L.result_bytes = ws ? ws->result_bytes : (budget * 3 / 10) / align * align;
+    L.work_bytes = ws ? ws->arena_bytes : (budget - L.result_bytes) / align * align;
+    L.split_rows = o.item_rows < 0 ? 0 : (o.item_rows > 0 ? (uint64_t)o.item_rows : 1024);
+    L.spill_bytes = L.split_rows ? (L.work_bytes / 4) / align * align : 0;
+    L.slices_bytes = L.work_bytes - L.spill_bytes;
+    int grid = L.nsm * per_sm;
+    while (grid > 1 && (L.slices_bytes / (uint64_t)grid) * 2 / 5 < min_table) grid /= 2;
+    L.grid = grid;
+    L.slice = (L.slices_bytes / (uint64_t)grid) / align * align;
+    L.s_bytes = (L.slice / 5) / align * align;
+    L.t_bytes = ((L.slice - L.s_bytes) / 2) / align * align;
+    if (L.t_bytes < min_table) {
+        L.all_plain = true;                 // too small for any slice: all on the plain path
         return GSI_OK;
     }
-    // seed words per item: at most one table region of seeds
-    const uint64_t max_words = std::max<uint64_t>(1, (t_bytes - 1024) / 128);
+    // per-query records, step configurations and seed units
+    std::vector<BatchQuery> bqs((size_t)nq);
+    std::vector<JoinArgs> cfg;
+    std::vector<BatchItem> items;
+    const uint64_t max_words = std::max<uint64_t>(1, (L.t_bytes - 1024) / 128);   // seeds fit a table region
     for (int i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
         std::memset(&bqs[i], 0, sizeof(BatchQuery));
@@ -418,13 +419,14 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
         bqs[i].count_only = o.count_only;
         if (!p.active) continue;
         bqs[i].seed_bm = p.bitmaps + (uint64_t)p.order[0] * (uint64_t)g->nwords;
+        bqs[i].cfg0 = (int32_t)cfg.size();
+        cfg.resize(cfg.size() + (size_t)p.k);
         for (int t = 1; t < p.k; ++t) {
             const int co = (t == p.k - 1) && o.count_only;
-            cfg[(size_t)i * GSI_MAX_QUERY_VERTICES + t] =
-                make_join_args(g, p.steps[t], p.bitmaps + (uint64_t)p.order[t] * (uint64_t)g->nwords, co, dstats);
+            cfg[(size_t)bqs[i].cfg0 + t] =
+                make_join_args(g, p.steps[t], p.bitmaps + (uint64_t)p.order[t] * (uint64_t)g->nwords, co, L.dstats);
         }
-        // split the seed bitmap into word ranges holding about seeds_per_item
-        // seeds each (and never more words than a table region can take)
+        // word ranges of the seed bitmap holding about seeds_per_item seeds each
         const uint64_t nw = (uint64_t)g->nwords;
         const uint64_t per = o.seeds_per_item > 0 ? (uint64_t)o.seeds_per_item : 32;
         uint64_t parts = std::max<uint64_t>((p.seed_count + per - 1) / per, (nw + max_words - 1) / max_words);
@@ -439,134 +441,144 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
             if (it.word_hi > it.word_lo) items.push_back(it);
         }
     }
-    // control block: [configs][queries][items][records][gather offsets][spill units][spill ready][ctl]
-    const uint64_t sq_cap = split_rows ? SPILL_SLOTS : 0;
-    const uint64_t rec_cap = items.size() + sq_cap;
+    if (cfg.empty()) cfg.resize(1);
+    L.nitems = items.size();
+    L.ncfg = cfg.size();
+    // control block: [configs][queries][query template][items][records][gather offsets][spill units][ready][ctl]
+    L.sq_cap = L.split_rows ? SPILL_SLOTS : 0;
+    L.rec_cap = items.size() + L.sq_cap;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t o_q = up(sizeof(JoinArgs) * cfg.size());
-    const size_t o_items = o_q + up(sizeof(BatchQuery) * bqs.size());
-    const size_t o_recs = o_items + up(sizeof(BatchItem) * items.size());
-    const size_t o_dst = o_recs + up(sizeof(BatchRec) * rec_cap);
-    const size_t o_sq = o_dst + up(sizeof(unsigned long long) * rec_cap);
-    const size_t o_ready = o_sq + up(sizeof(SpillUnit) * sq_cap);
-    const size_t o_ctl = o_ready + up(sizeof(unsigned) * sq_cap);
-    const size_t ctl_bytes = o_ctl + up(sizeof(BatchCtl));
-    unsigned char *ctl = nullptr, *arena = nullptr;
-    int32_t *result = nullptr;
-    auto free_all = [&]() {
-        if (ctl) cudaFreeAsync(ctl, st);
-        if (!ws && arena) cudaFreeAsync(arena, st);
-        if (!ws && result) cudaFreeAsync(result, st);
-        if (dstats) cudaFreeAsync(dstats, st);
-    };
-    if (ws) {
-        arena = ws->arena;
-        result = ws->result;
-    }
-    if (cudaMallocAsync(&ctl, ctl_bytes, st) != cudaSuccess ||
-        (!ws && cudaMallocAsync(&arena, work_bytes, st) != cudaSuccess) ||
-        (!ws && cudaMallocAsync(&result, result_bytes, st) != cudaSuccess)) {
-        free_all();
+    L.o_q = up(sizeof(JoinArgs) * cfg.size());
+    L.o_tpl = L.o_q + up(sizeof(BatchQuery) * bqs.size());
+    L.o_items = L.o_tpl + (keep_template ? up(sizeof(BatchQuery) * bqs.size()) : 0);
+    L.o_recs = L.o_items + up(sizeof(BatchItem) * items.size());
+    L.o_dst = L.o_recs + up(sizeof(BatchRec) * L.rec_cap);
+    L.o_sq = L.o_dst + up(sizeof(unsigned long long) * L.rec_cap);
+    L.o_ready = L.o_sq + up(sizeof(SpillUnit) * L.sq_cap);
+    L.o_ctl = L.o_ready + up(sizeof(unsigned) * L.sq_cap);
+    L.ctl_bytes = L.o_ctl + up(sizeof(BatchCtl));
+    L.has_template = keep_template;
+    if (cudaMallocAsync(&L.ctl, L.ctl_bytes, st) != cudaSuccess) {
         (void)cudaGetLastError();
-        set_error("batch: could not reserve the batch arena");
+        L.ctl = nullptr;
+        set_error("batch: could not reserve the control block");
         return GSI_ENOMEM;
     }
-    JoinArgs *d_cfg = reinterpret_cast<JoinArgs *>(ctl);
-    BatchQuery *d_q = reinterpret_cast<BatchQuery *>(ctl + o_q);
-    BatchItem *d_items = reinterpret_cast<BatchItem *>(ctl + o_items);
-    BatchRec *d_recs = reinterpret_cast<BatchRec *>(ctl + o_recs);
-    unsigned long long *d_dst = reinterpret_cast<unsigned long long *>(ctl + o_dst);
-    SpillUnit *d_sq = reinterpret_cast<SpillUnit *>(ctl + o_sq);
-    unsigned *d_ready = reinterpret_cast<unsigned *>(ctl + o_ready);
-    BatchCtl *d_ctl = reinterpret_cast<BatchCtl *>(ctl + o_ctl);
-    BatchCtl hctl;
-    std::memset(&hctl, 0, sizeof hctl);
-    hctl.pending = items.size();
-    gsi_status rc = GSI_OK;
-    if (cudaMemcpyAsync(d_cfg, cfg.data(), sizeof(JoinArgs) * cfg.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(d_q, bqs.data(), sizeof(BatchQuery) * bqs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        (items.size() && cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * items.size(),
-                                         cudaMemcpyHostToDevice, st) != cudaSuccess) ||
-        (sq_cap && cudaMemsetAsync(d_ready, 0, sizeof(unsigned) * sq_cap, st) != cudaSuccess) ||
-        cudaMemcpyAsync(d_ctl, &hctl, sizeof hctl, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        set_error("batch: control upload failed");
-        rc = GSI_ECUDA;
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (stats) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventRecord(e0, st);
-    }
-    if (rc == GSI_OK && !items.empty()) {
-        BatchArgs ba;
-        ba.cfgs = d_cfg;
-        ba.queries = d_q;
-        ba.items = d_items;
-        ba.nitems = (int64_t)items.size();
-        ba.recs = d_recs;
-        ba.sq = d_sq;
-        ba.sq_ready = d_ready;
-        ba.sq_cap = sq_cap;
-        ba.spill = reinterpret_cast<int32_t *>(arena + slices_bytes);
-        ba.spill_cap = spill_bytes / 4;
-        ba.ctl = d_ctl;
-        ba.result = result;
-        ba.result_cap = result_bytes / 4;
-        ba.arena = arena;
-        ba.slice_bytes = slice;
-        ba.s_bytes = s_bytes;
-        ba.t_bytes = t_bytes;
-        ba.split_rows = split_rows;
-        ba.spin_limit = WAIT_SPIN_LIMIT;
-        k_batch<<<grid, BNT, sm, st>>>(ba);
-        if (cudaGetLastError() != cudaSuccess) {
-            set_error("batch: kernel launch failed");
-            rc = GSI_ECUDA;
+    if (ws) {
+        L.arena = ws->arena;
+    } else {
+        if (cudaMallocAsync(&L.arena, L.work_bytes, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            L.arena = nullptr;
+            set_error("batch: could not reserve the batch arena");
+            return GSI_ENOMEM;
         }
+        L.own_arena = true;
     }
-    if (stats) cudaEventRecord(e1, st);
-    // read back the control block, the queries and the unit records
+    GSI_CUDA_TRY(cudaMemcpyAsync(L.ctl, cfg.data(), sizeof(JoinArgs) * cfg.size(), cudaMemcpyHostToDevice, st));
+    if (items.size())
+        GSI_CUDA_TRY(cudaMemcpyAsync(L.ctl + L.o_items, items.data(), sizeof(BatchItem) * items.size(),
+                                     cudaMemcpyHostToDevice, st));
+    if (keep_template)
+        GSI_CUDA_TRY(cudaMemcpyAsync(L.ctl + L.o_tpl, bqs.data(), sizeof(BatchQuery) * bqs.size(),
+                                     cudaMemcpyHostToDevice, st));
+    L.q_init.assign(reinterpret_cast<const unsigned char *>(bqs.data()),
+                    reinterpret_cast<const unsigned char *>(bqs.data()) + sizeof(BatchQuery) * bqs.size());
+    return GSI_OK;
+}
+
+// The launch's control words: counters zeroed, every seed unit pending, the
+// result arena (host to device, ahead of the kernel on the stream).
+gsi_status batch_enqueue_ctl(BatchLaunch &L, int32_t *result, uint64_t result_bytes, cudaStream_t st) {
+    if (L.all_plain) return GSI_OK;
+    BatchCtl h;
+    std::memset(&h, 0, sizeof h);
+    h.result = result;
+    h.result_cap = result_bytes / 4;
+    h.pending = L.nitems;
+    GSI_CUDA_TRY(cudaMemcpyAsync(L.ctl + L.o_ctl, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    return GSI_OK;
+}
+
+// Query records reset, spill queue cleared, counters zeroed, then the kernel.
+// With a template every step is device work only, so it can be captured.
+gsi_status batch_enqueue_kernel(BatchLaunch &L, cudaStream_t st) {
+    if (L.all_plain) return GSI_OK;
+    BatchQuery *d_q = reinterpret_cast<BatchQuery *>(L.ctl + L.o_q);
+    if (L.has_template)
+        GSI_CUDA_TRY(cudaMemcpyAsync(d_q, L.ctl + L.o_tpl, L.q_init.size(), cudaMemcpyDeviceToDevice, st));
+    else
+        GSI_CUDA_TRY(cudaMemcpyAsync(d_q, L.q_init.data(), L.q_init.size(), cudaMemcpyHostToDevice, st));
+    if (L.sq_cap) GSI_CUDA_TRY(cudaMemsetAsync(L.ctl + L.o_ready, 0, sizeof(unsigned) * L.sq_cap, st));
+    if (L.dstats) GSI_CUDA_TRY(cudaMemsetAsync(L.dstats, 0, 16, st));
+    if (L.nitems == 0) return GSI_OK;
+    BatchArgs ba;
+    ba.cfgs = reinterpret_cast<const JoinArgs *>(L.ctl);
+    ba.queries = d_q;
+    ba.items = reinterpret_cast<const BatchItem *>(L.ctl + L.o_items);
+    ba.nitems = (int64_t)L.nitems;
+    ba.recs = reinterpret_cast<BatchRec *>(L.ctl + L.o_recs);
+    ba.sq = reinterpret_cast<SpillUnit *>(L.ctl + L.o_sq);
+    ba.sq_ready = reinterpret_cast<unsigned *>(L.ctl + L.o_ready);
+    ba.sq_cap = L.sq_cap;
+    ba.spill = reinterpret_cast<int32_t *>(L.arena + L.slices_bytes);
+    ba.spill_cap = L.spill_bytes / 4;
+    ba.ctl = reinterpret_cast<BatchCtl *>(L.ctl + L.o_ctl);
+    ba.arena = L.arena;
+    ba.slice_bytes = L.slice;
+    ba.s_bytes = L.s_bytes;
+    ba.t_bytes = L.t_bytes;
+    ba.split_rows = L.split_rows;
+    ba.spin_limit = WAIT_SPIN_LIMIT;
+    k_batch<<<L.grid, BNT, L.sm, st>>>(ba);
+    GSI_CUDA_TRY(cudaGetLastError());
+    return GSI_OK;
+}
+
+// After the kernel: each plan's count, failed flag and row chunks.  With a
+// workspace the kept rows are gathered into one tight buffer; otherwise the
+// chunks point into `result`, which `arena` (when given) keeps alive.
+gsi_status batch_collect(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &plans, int32_t *result,
+                         std::shared_ptr<ResultArena> arena, cudaStream_t st, gsi_stats *stats, BatchWorkspace *ws) {
+    const int nq = (int)plans.size();
+    for (BatchPlan &p : plans) {
+        p.failed = false;
+        p.count = 0;
+        p.chunks.clear();
+        p.arena.reset();
+    }
+    if (L.all_plain) {
+        for (BatchPlan &p : plans)
+            if (p.active) p.failed = true;
+        return GSI_OK;
+    }
     BatchCtl rctl;
     std::memset(&rctl, 0, sizeof rctl);
+    std::vector<BatchQuery> bqs((size_t)nq);
     std::vector<BatchRec> recs;
-    if (rc == GSI_OK) {
-        if (cudaMemcpyAsync(&rctl, d_ctl, sizeof rctl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(bqs.data(), d_q, sizeof(BatchQuery) * bqs.size(), cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            set_error("batch: kernel or readback failed");
-            rc = GSI_ECUDA;
-        }
+    BatchQuery *d_q = reinterpret_cast<BatchQuery *>(L.ctl + L.o_q);
+    if (cudaMemcpyAsync(&rctl, L.ctl + L.o_ctl, sizeof rctl, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(bqs.data(), d_q, sizeof(BatchQuery) * bqs.size(), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("batch: kernel or readback failed");
+        return GSI_ECUDA;
     }
-    if (rc == GSI_OK && rctl.nrecs) {
+    if (rctl.nrecs) {
         recs.resize(rctl.nrecs);
-        if (cudaMemcpyAsync(recs.data(), d_recs, sizeof(BatchRec) * recs.size(), cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
+        if (cudaMemcpyAsync(recs.data(), L.ctl + L.o_recs, sizeof(BatchRec) * recs.size(), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             set_error("batch: record readback failed");
-            rc = GSI_ECUDA;
+            return GSI_ECUDA;
         }
     }
-    if (stats && e0) {
-        float ms = 0;
+    if (stats) {
         unsigned long long hb[2] = {0, 0};
-        if (rc == GSI_OK) {
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (cudaMemcpy(hb, dstats, 16, cudaMemcpyDeviceToHost) != cudaSuccess) hb[0] = hb[1] = 0;
-        }
-        stats->join_ms += ms;
-        stats->join_launches += items.empty() ? 0 : 1;
-        stats->kernels += items.empty() ? 0 : 1;
+        if (L.dstats && cudaMemcpy(hb, L.dstats, 16, cudaMemcpyDeviceToHost) != cudaSuccess) hb[0] = hb[1] = 0;
         stats->join_bytes += hb[0];
         stats->join_items += hb[1];
         stats->tiles += rctl.units;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
-    if (rc != GSI_OK) {
-        free_all();
-        return rc;
     }
     // a wait that ran out leaves units undone: every query goes to the plain path
     const bool all_failed = rctl.error != 0;
@@ -597,15 +609,19 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
             fill[r.q] += r.rows * (uint64_t)plans[r.q].k;
         }
         int32_t *buf = nullptr;
+        gsi_status rc = GSI_OK;
         if (tot > 0) {
+            unsigned long long *d_dst = reinterpret_cast<unsigned long long *>(L.ctl + L.o_dst);
             if (cudaMallocAsync(&buf, tot * 4, st) != cudaSuccess ||
                 cudaMemcpyAsync(d_dst, dst.data(), sizeof(unsigned long long) * dst.size(), cudaMemcpyHostToDevice,
                                 st) != cudaSuccess) {
+                (void)cudaGetLastError();
                 set_error("batch: result buffer or gather upload failed");
                 rc = GSI_ENOMEM;
             } else {
-                const int gblocks = (int)std::min<size_t>(recs.size(), (size_t)nsm * 8);
-                k_gather<<<gblocks, 256, 0, st>>>(d_q, d_recs, d_dst, result, buf, (int64_t)recs.size());
+                const int gblocks = (int)std::min<size_t>(recs.size(), (size_t)L.nsm * 8);
+                k_gather<<<gblocks, 256, 0, st>>>(d_q, reinterpret_cast<const BatchRec *>(L.ctl + L.o_recs), d_dst,
+                                                  result, buf, (int64_t)recs.size());
                 if (stats) {
                     stats->kernels += 1;
                     stats->other_launches += 1;
@@ -632,23 +648,67 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
         } else if (buf) {
             cudaFreeAsync(buf, st);
         }
-        free_all();
         return rc;
     }
-    // results: chunks point into the shared result arena, which the last
-    // result to be destroyed releases
-    auto shared = std::make_shared<ResultArena>();
-    shared->ptr = result;
-    shared->device = g->device;
-    shared->stream = st;
-    shared->own_stream = true;
-    result = nullptr;
     for (const BatchRec &r : recs)
-        if (!plans[r.q].failed) plans[r.q].chunks.push_back({shared->ptr + r.off, r.rows});
+        if (!plans[r.q].failed) plans[r.q].chunks.push_back({result + r.off, r.rows});
     for (int i = 0; i < nq; ++i)
-        if (plans[i].active) plans[i].arena = shared;
-    free_all();
+        if (plans[i].active) plans[i].arena = arena;
     return GSI_OK;
+}
+
+void batch_release(BatchLaunch &L, cudaStream_t st) {
+    if (L.ctl) cudaFreeAsync(L.ctl, st);
+    if (L.own_arena && L.arena) cudaFreeAsync(L.arena, st);
+    if (L.dstats) cudaFreeAsync(L.dstats, st);
+    L = BatchLaunch();
+}
+
+// One batch launch end to end: setup, control words, kernel, collection.
+gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o,
+                            uint64_t budget, cudaStream_t st, gsi_stats *stats, BatchWorkspace *ws) {
+    if (plans.empty()) return GSI_OK;
+    BatchLaunch L;
+    gsi_status rc = batch_setup(L, g, plans, o, budget, st, ws, stats != nullptr, false);
+    int32_t *result = nullptr;
+    std::shared_ptr<ResultArena> arena;
+    if (rc == GSI_OK && !L.all_plain) {
+        if (ws) {
+            result = ws->result;
+        } else if (cudaMallocAsync(&result, L.result_bytes, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            result = nullptr;
+            set_error("batch: could not reserve the result arena");
+            rc = GSI_ENOMEM;
+        } else {
+            arena = std::make_shared<ResultArena>();     // the last result to go releases it
+            arena->ptr = result;
+            arena->device = g->device;
+            arena->stream = st;
+            arena->own_stream = true;
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == GSI_OK && stats && !L.all_plain) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+    }
+    if (rc == GSI_OK) rc = batch_enqueue_ctl(L, result, L.result_bytes, st);
+    if (rc == GSI_OK && e0) cudaEventRecord(e0, st);
+    if (rc == GSI_OK) rc = batch_enqueue_kernel(L, st);
+    if (rc == GSI_OK && e1) cudaEventRecord(e1, st);
+    if (rc == GSI_OK) rc = batch_collect(L, g, plans, result, arena, st, stats, ws);
+    if (e0) {
+        float ms = 0;
+        if (rc == GSI_OK) cudaEventElapsedTime(&ms, e0, e1);
+        stats->join_ms += ms;
+        stats->join_launches += L.nitems ? 1 : 0;
+        stats->kernels += L.nitems ? 1 : 0;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    batch_release(L, st);
+    return rc;
 }
 
 }  // namespace gsi

@@ -134,6 +134,16 @@ __global__ void k_sig_pairs(const int32_t *__restrict__ src, const int32_t *__re
     }
 }
 
+// Words 1..15 of every grouped position's vertex (zero for padding).
+__global__ void k_group_sig(const uint32_t *__restrict__ sig, int32_t n, const int32_t *__restrict__ gperm,
+                            int64_t np, uint32_t *__restrict__ gsig) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = gperm[p];
+#pragma unroll
+        for (int w = 1; w < GSI_SIG_WORDS; ++w) gsig[(int64_t)(w - 1) * np + p] = v >= 0 ? sig[(int64_t)w * n + v] : 0u;
+    }
+}
+
 __global__ void k_label_hist(const int32_t *__restrict__ elab, int64_t m, int32_t L, unsigned long long *freq) {
     extern __shared__ unsigned long long h[];
     const bool local = L <= 4096;
@@ -247,6 +257,22 @@ gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32
         return GSI_EINVAL;
     }
 
+    // vertices grouped by label rank (host counting sort, ascending ids per
+    // group, each group padded to a multiple of 32 positions)
+    std::vector<int32_t> gperm;
+    std::vector<int64_t> goff((size_t)LV + 1, 0);
+    {
+        std::vector<int32_t> rank((size_t)n);
+        for (int32_t v = 0; v < n; ++v)
+            rank[v] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), vlab[v]) - uniq.begin());
+        std::vector<int64_t> cnt((size_t)LV, 0);
+        for (int32_t v = 0; v < n; ++v) ++cnt[rank[v]];
+        for (int32_t r = 0; r < LV; ++r) goff[r + 1] = goff[r] + (cnt[r] + 31) / 32 * 32;
+        gperm.assign((size_t)goff[LV], -1);
+        std::vector<int64_t> pos(goff.begin(), goff.end() - 1);
+        for (int32_t v = 0; v < n; ++v) gperm[pos[rank[v]]++] = v;
+    }
+
     // duplicate vertex pairs
     uint64_t *keys = nullptr, *tmp = nullptr;
     GSI_CUDA_TRY(cudaMallocAsync(&keys, sizeof(uint64_t) * (size_t)(2 * m + 1), st));
@@ -295,6 +321,14 @@ gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32
     k_sig_labels<<<grid_for(n), NT, 0, st>>>(d_vlab, n, g->sig);
     if (m > 0) k_sig_pairs<<<grid_for(2 * m), NT, 0, st>>>(d_src, d_dst, d_elab, d_vlab, m, n, g->sig);
 
+    // signatures grouped by label
+    g->np = goff[LV];
+    g->goff = goff;
+    GSI_CUDA_TRY(cudaMallocAsync(&g->gperm, sizeof(int32_t) * (size_t)g->np, st));
+    GSI_CUDA_TRY(cudaMallocAsync(&g->gsig, sizeof(uint32_t) * (size_t)(GSI_SIG_WORDS - 1) * (size_t)g->np, st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(g->gperm, gperm.data(), sizeof(int32_t) * (size_t)g->np, cudaMemcpyHostToDevice, st));
+    k_group_sig<<<grid_for(g->np), NT, 0, st>>>(g->sig, n, g->gperm, g->np, g->gsig);
+
     // freq(l)
     unsigned long long *d_freq = nullptr;
     GSI_CUDA_TRY(cudaMallocAsync(&d_freq, sizeof(unsigned long long) * (size_t)L, st));
@@ -316,7 +350,8 @@ gsi_status build_graph(gsi_graph *g, const int32_t *vlab, int32_t n, const int32
     cudaEventDestroy(e1);
     g->build_ms = ms;
     g->device_bytes = sizeof(uint32_t) * (nseg + 1) + sizeof(int32_t) * (uint64_t)(2 * m + 1) +
-                      sizeof(uint16_t) * (uint64_t)(2 * m + 1) + sizeof(uint32_t) * GSI_SIG_WORDS * (uint64_t)n;
+                      sizeof(uint16_t) * (uint64_t)(2 * m + 1) + sizeof(uint32_t) * GSI_SIG_WORDS * (uint64_t)n +
+                      sizeof(uint32_t) * GSI_SIG_WORDS * (uint64_t)g->np;
     return GSI_OK;
 }
 

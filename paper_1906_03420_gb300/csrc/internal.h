@@ -20,6 +20,14 @@ struct gsi_graph {
     int32_t *ci = nullptr;      // [2m], each N(v,l) sorted by (label rank of neighbour, id)
     uint16_t *cl = nullptr;     // [2m], label rank of ci[p]
     uint32_t *sig = nullptr;    // [16 * n], column-first
+    // the same signatures grouped by vertex label: gperm holds the vertex ids
+    // of each label rank in ascending order, every group padded with -1 to a
+    // multiple of 32 positions (goff: first position of each group); gsig holds
+    // words 1..15 of gperm[p] at gsig[(w - 1) * np + p] (0 for padding)
+    int32_t *gperm = nullptr;   // [np]
+    uint32_t *gsig = nullptr;   // [15 * np]
+    int64_t np = 0;
+    std::vector<int64_t> goff;  // [LV + 1]
     std::vector<uint64_t> freq; // [L]
     std::vector<int32_t> vlabels;   // sorted distinct vertex labels; rank = index
     int32_t label_rank(int32_t label) const;   // -1 if no vertex carries it
@@ -46,13 +54,30 @@ struct QuerySig {
 };
 void query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
                       const int32_t *qelab, int32_t qm, QuerySig *out);
-// bitmaps: device uint32[k][nwords]; counts: device unsigned long long[k] (zeroed here).
+// bitmaps: device uint32[k][nwords]; counts: device unsigned long long[k] (both zeroed here).
 gsi_status launch_filter(const gsi_graph *g, const QuerySig &q, uint32_t *bitmaps, unsigned long long *counts,
                          cudaStream_t st);
 // Every query vertex of a batch in one pass: bitmaps [sum k][nwords] and
 // counts [sum k] in query order (zeroed here).
 gsi_status launch_filter_batch(const gsi_graph *g, const std::vector<QuerySig> &qs, uint32_t *bitmaps,
                                unsigned long long *counts, cudaStream_t st);
+// A filter call split in two: filter_plan groups the query vertices by label
+// and uploads their signatures (host work, stream-ordered allocation);
+// filter_enqueue zeroes bitmaps [nqv][nwords] and counters [nqv] and runs the
+// kernel (stream work only: capturable into a CUDA graph).
+struct FilterPlan {
+    uint32_t *d_q = nullptr;    // grouped signatures, then the group table
+    int32_t *d_meta = nullptr;
+    int32_t nqv = 0, nq = 0, ngroups = 0;
+    int64_t warps = 0;
+};
+gsi_status filter_plan(const gsi_graph *g, const std::vector<const uint32_t *> &sigs, FilterPlan *fp,
+                       cudaStream_t st);
+gsi_status filter_enqueue(const gsi_graph *g, const FilterPlan &fp, uint32_t *bitmaps, unsigned long long *counts,
+                          cudaStream_t st);
+void filter_plan_free(FilterPlan &fp, cudaStream_t st);
+// Algorithmic bytes of one filter call over query vertices with these labels.
+uint64_t filter_alg_bytes(const gsi_graph *g, const std::vector<int32_t> &labels);
 // Compact the bitmap of C(u) into the int32 list out (ascending); scratch: uint32[scan_blocks+1].
 gsi_status launch_seed(const gsi_graph *g, const uint32_t *bitmap, int32_t *out, uint32_t *scratch,
                        cudaStream_t st);

@@ -692,7 +692,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         for (int p = 0; p < q.k; ++p) s->order[p] = (rc == GSI_OK && !empty) ? order[p] : -1;
         s->tiles += x.tiles;
         s->peak_bytes = std::max<uint64_t>(s->peak_bytes, x.peak);
-        s->filter_bytes += (uint64_t)g->n * (4 + 60) + bm_words * 4;
+        s->filter_bytes += filter_alg_bytes(g, std::vector<int32_t>(q.vlab, q.vlab + q.k));
         s->join_bytes += x.join_bytes;
         s->join_items += x.join_items;
         s->kernels += x.kernels;

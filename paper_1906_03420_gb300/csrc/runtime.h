@@ -121,6 +121,50 @@ struct BatchWorkspace {
     uint64_t result_bytes = 0;
 };
 
+// One k_batch launch (batch.cu): sizing, the device control block and the
+// work area.  batch_setup reserves and uploads what stays fixed;
+// batch_enqueue_ctl writes the launch's control words (host to device);
+// batch_enqueue_kernel resets the query records and runs the kernel (device
+// work only when the launch keeps a template, hence capturable);
+// batch_collect reads the outcome back into the plans.
+struct BatchLaunch {
+    int grid = 0, nsm = 152;
+    size_t sm = 0;
+    uint64_t result_bytes = 0, work_bytes = 0, spill_bytes = 0, slices_bytes = 0;
+    uint64_t slice = 0, s_bytes = 0, t_bytes = 0, split_rows = 0, sq_cap = 0, rec_cap = 0;
+    size_t nq = 0, nitems = 0, ncfg = 0;
+    size_t o_q = 0, o_tpl = 0, o_items = 0, o_recs = 0, o_dst = 0, o_sq = 0, o_ready = 0, o_ctl = 0, ctl_bytes = 0;
+    unsigned char *ctl = nullptr;            // control block
+    unsigned char *arena = nullptr;          // work area: per-CTA slices, then the spill area
+    bool own_arena = false;
+    unsigned long long *dstats = nullptr;    // algorithmic bytes and candidates (optional)
+    bool all_plain = false;                  // the budget holds no slice: every query on the plain path
+    bool has_template = false;               // the initial query records also live on the device
+    std::vector<unsigned char> q_init;       // initial query records
+};
+gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &o,
+                       uint64_t budget, cudaStream_t st, BatchWorkspace *ws, bool stats, bool keep_template);
+gsi_status batch_enqueue_ctl(BatchLaunch &L, int32_t *result, uint64_t result_bytes, cudaStream_t st);
+gsi_status batch_enqueue_kernel(BatchLaunch &L, cudaStream_t st);
+gsi_status batch_collect(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &plans, int32_t *result,
+                         std::shared_ptr<ResultArena> arena, cudaStream_t st, gsi_stats *stats, BatchWorkspace *ws);
+void batch_release(BatchLaunch &L, cudaStream_t st);
+
+// The filter outputs and planning inputs of a batch (serve.cu).
+struct BatchInputs {
+    uint32_t *bitmaps = nullptr;             // [sum of active k][nwords]
+    unsigned long long *counts = nullptr;
+    FilterPlan fp;
+    uint64_t nk = 0;
+    std::vector<int32_t> labels;             // query vertex labels (filter bytes)
+};
+gsi_status batch_plan_all(gsi_graph *g, std::vector<BatchPlan> &plans, gsi_stats *stats, cudaStream_t st,
+                          BatchInputs &in);
+void batch_inputs_free(BatchInputs &in, cudaStream_t st);
+gsi_status batch_finish(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo, uint64_t budget,
+                        cudaStream_t st, std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses);
+uint64_t batch_budget(const gsi_batch_opts &bo);
+
 gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
                          std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses,
                          BatchWorkspace *ws = nullptr);

@@ -25,24 +25,20 @@ using namespace gsi;
 // the batch arena run again on the plain path.  Invalid queries carry their
 // status in plans[i].status.
 namespace gsi {
-gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
-                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses, BatchWorkspace *ws) {
+// The first half of a batch: queries that cannot match (a label no data
+// vertex or edge carries) become inactive, one filter pass covers every query
+// vertex of the rest, and each query with non-empty candidate sets gets its
+// Alg. 2 order and steps.  The bitmaps stay allocated in `in` (the join reads
+// them) until batch_inputs_free.
+gsi_status batch_plan_all(gsi_graph *g, std::vector<BatchPlan> &plans, gsi_stats *stats, cudaStream_t st,
+                          BatchInputs &in) {
     const int32_t nq = (int32_t)plans.size();
-    outs.assign((size_t)nq, nullptr);
-    statuses.assign((size_t)nq, GSI_OK);
-    GSI_TRY(prepare_device(g->device));
-    cudaStream_t st = (cudaStream_t)bo.stream;
-    uint64_t budget = bo.mem_budget;
-    if (!budget) {
-        size_t fr = 0, tot = 0;
-        GSI_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-        budget = (uint64_t)(0.4 * (double)tot);
-    }
     std::vector<int32_t> ranks((size_t)nq * GSI_MAX_QUERY_VERTICES, 0);
     uint64_t bm_words = 0, nk = 0;
     std::vector<uint64_t> bm_off((size_t)nq, 0), k_off((size_t)nq, 0);
     for (int32_t i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
+        p.active = false;
         if (p.status != GSI_OK) continue;
         p.k = p.q.k;
         bool empty = (p.k > 1 && g->m == 0);
@@ -58,55 +54,50 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
         bm_words += (uint64_t)p.k * (uint64_t)g->nwords;
         nk += (uint64_t)p.k;
     }
-    uint32_t *bitmaps = nullptr;
-    unsigned long long *counts = nullptr;
-    if (nk) {
-        GSI_CUDA_TRY(cudaMallocAsync(&bitmaps, bm_words * 4 + 16, st));
-        GSI_CUDA_TRY(cudaMallocAsync(&counts, nk * 8, st));
+    in.nk = nk;
+    if (nk == 0) return GSI_OK;
+    GSI_CUDA_TRY(cudaMallocAsync(&in.bitmaps, bm_words * 4 + 16, st));
+    GSI_CUDA_TRY(cudaMallocAsync(&in.counts, nk * 8, st));
+    std::vector<QuerySig> sigs;
+    sigs.reserve((size_t)nq);
+    for (int32_t i = 0; i < nq; ++i) {
+        BatchPlan &p = plans[i];
+        if (!p.active) continue;
+        sigs.emplace_back();
+        query_signatures(p.q.vl.data(), p.k, p.q.src.data(), p.q.dst.data(), p.q.lab.data(), p.q.qm, &sigs.back());
+        p.bitmaps = in.bitmaps + bm_off[i];
+        in.labels.insert(in.labels.end(), p.q.vlab, p.q.vlab + p.k);
     }
-    gsi_status rc = GSI_OK;
+    std::vector<const uint32_t *> sp;
+    for (const QuerySig &q : sigs)
+        for (int u = 0; u < q.k; ++u) sp.push_back(q.sig[u]);
+    GSI_TRY(filter_plan(g, sp, &in.fp, st));
     cudaEvent_t f0 = nullptr, f1 = nullptr;
-    if (bo.stats) {
+    if (stats) {
         cudaEventCreate(&f0);
         cudaEventCreate(&f1);
         cudaEventRecord(f0, st);
     }
-    uint64_t nfilters = 0;
-    {
-        std::vector<QuerySig> sigs;
-        for (int32_t i = 0; i < nq; ++i) {
-            BatchPlan &p = plans[i];
-            if (!p.active) continue;
-            sigs.emplace_back();
-            query_signatures(p.q.vl.data(), p.k, p.q.src.data(), p.q.dst.data(), p.q.lab.data(), p.q.qm,
-                             &sigs.back());
-            p.bitmaps = bitmaps + bm_off[i];
-        }
-        if (!sigs.empty()) {
-            rc = launch_filter_batch(g, sigs, bitmaps, counts, st);
-            nfilters = 1;
-        }
-    }
-    if (bo.stats) cudaEventRecord(f1, st);
+    gsi_status rc = filter_enqueue(g, in.fp, in.bitmaps, in.counts, st);
+    if (stats) cudaEventRecord(f1, st);
     std::vector<uint64_t> hc(nk);
-    if (rc == GSI_OK && nk) {
-        if (cudaMemcpyAsync(hc.data(), counts, nk * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            set_error("batch: filter readback failed");
-            rc = GSI_ECUDA;
-        }
+    if (rc == GSI_OK && (cudaMemcpyAsync(hc.data(), in.counts, nk * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess)) {
+        set_error("batch: filter readback failed");
+        rc = GSI_ECUDA;
     }
-    if (bo.stats && f0) {
+    if (stats) {
         float ms = 0;
         if (rc == GSI_OK) cudaEventElapsedTime(&ms, f0, f1);
-        bo.stats->filter_ms += ms;
-        bo.stats->filter_launches += nfilters;
-        bo.stats->kernels += nfilters;
-        bo.stats->filter_bytes += nfilters * ((uint64_t)g->n * 64 + bm_words * 4);
+        stats->filter_ms += ms;
+        stats->filter_launches += 1;
+        stats->kernels += 1;
+        stats->filter_bytes += filter_alg_bytes(g, in.labels);
         cudaEventDestroy(f0);
         cudaEventDestroy(f1);
     }
-    for (int32_t i = 0; i < nq && rc == GSI_OK; ++i) {
+    if (rc != GSI_OK) return rc;
+    for (int32_t i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
         if (!p.active) continue;
         const uint64_t *c = hc.data() + k_off[i];
@@ -118,10 +109,23 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
         }
         plan_for_batch(g, p, c, ranks.data() + (size_t)i * GSI_MAX_QUERY_VERTICES);
     }
-    if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats, ws);
-    if (bitmaps) cudaFreeAsync(bitmaps, st);
-    if (counts) cudaFreeAsync(counts, st);
-    if (rc != GSI_OK) return rc;
+    return GSI_OK;
+}
+
+void batch_inputs_free(BatchInputs &in, cudaStream_t st) {
+    if (in.bitmaps) cudaFreeAsync(in.bitmaps, st);
+    if (in.counts) cudaFreeAsync(in.counts, st);
+    filter_plan_free(in.fp, st);
+    in = BatchInputs();
+}
+
+// The second half: a result object per query from its plan (rows in the
+// batch's shared buffer), or a rerun on the plain path for a failed query.
+gsi_status batch_finish(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo, uint64_t budget,
+                        cudaStream_t st, std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses) {
+    const int32_t nq = (int32_t)plans.size();
+    outs.assign((size_t)nq, nullptr);
+    statuses.assign((size_t)nq, GSI_OK);
     gsi_status first_err = GSI_OK;
     for (int32_t i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
@@ -129,7 +133,7 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
         if (qrc == GSI_OK && p.active && p.failed) {
             gsi_query_opts o;
             std::memset(&o, 0, sizeof o);
-            o.stream = bo.stream;
+            o.stream = st;
             o.row_cap = bo.row_cap;
             o.mem_budget = budget;
             o.count_only = bo.count_only;
@@ -159,6 +163,29 @@ gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_
         if (qrc != GSI_OK && qrc != GSI_EINVAL && first_err == GSI_OK) first_err = qrc;
     }
     return first_err;
+}
+
+uint64_t batch_budget(const gsi_batch_opts &bo) {
+    if (bo.mem_budget) return bo.mem_budget;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    return (uint64_t)(0.4 * (double)tot);
+}
+
+gsi_status batch_execute(gsi_graph *g, std::vector<BatchPlan> &plans, const gsi_batch_opts &bo,
+                         std::vector<gsi_result *> &outs, std::vector<gsi_status> &statuses, BatchWorkspace *ws) {
+    const int32_t nq = (int32_t)plans.size();
+    outs.assign((size_t)nq, nullptr);
+    statuses.assign((size_t)nq, GSI_OK);
+    GSI_TRY(prepare_device(g->device));
+    cudaStream_t st = (cudaStream_t)bo.stream;
+    const uint64_t budget = batch_budget(bo);
+    BatchInputs in;
+    gsi_status rc = batch_plan_all(g, plans, bo.stats, st, in);
+    if (rc == GSI_OK) rc = batch_run_device(g, plans, bo, budget, st, bo.stats, ws);
+    batch_inputs_free(in, st);
+    if (rc != GSI_OK) return rc;
+    return batch_finish(g, plans, bo, budget, st, outs, statuses);
 }
 }  // namespace gsi
 
@@ -191,7 +218,8 @@ extern "C" gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int3
 }
 
 extern "C" gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs, int32_t nq,
-                                         const gsi_batch_opts *opts, int32_t *best_seeds_per_item, double *best_ms) {
+                                         const gsi_batch_opts *opts, int32_t *best_seeds_per_item,
+                                         int32_t *best_item_rows, double *best_ms) {
     if (!g || nq < 1 || !qs) {
         set_error("gsi_batch_autotune: need a graph and at least one query");
         return GSI_EINVAL;
@@ -205,34 +233,40 @@ extern "C" gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs,
         for (int32_t i = 0; i < nq; ++i)
             proto[i].status = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm,
                                              &proto[i].q);
-        const int32_t cand[] = {16, 32, 64, 128, 256};
+        const int32_t cand_spi[] = {32, 64, 128};
+        const int32_t cand_rows[] = {512, 1024, 2048};
         double best = 1e300;
-        int32_t arg = 32;
-        for (int32_t c : cand) {
-            double t_best = 1e300;
-            for (int rep = 0; rep < 2; ++rep) {
-                std::vector<BatchPlan> plans((size_t)nq);
-                for (int32_t i = 0; i < nq; ++i) {
-                    plans[i].status = proto[i].status;
-                    plans[i].q = proto[i].q;
+        int32_t arg_spi = 32, arg_rows = 1024;
+        for (int32_t spi : cand_spi) {
+            for (int32_t rows : cand_rows) {
+                double t_best = 1e300;
+                for (int rep = 0; rep < 2; ++rep) {
+                    std::vector<BatchPlan> plans((size_t)nq);
+                    for (int32_t i = 0; i < nq; ++i) {
+                        plans[i].status = proto[i].status;
+                        plans[i].q = proto[i].q;
+                    }
+                    bo.seeds_per_item = spi;
+                    bo.item_rows = rows;
+                    std::vector<gsi_result *> res;
+                    std::vector<gsi_status> sts;
+                    auto t0 = std::chrono::steady_clock::now();
+                    gsi_status rc = batch_execute(g, plans, bo, res, sts);
+                    if (bo.stream) cudaStreamSynchronize((cudaStream_t)bo.stream);
+                    auto t1 = std::chrono::steady_clock::now();
+                    for (gsi_result *r : res) delete r;
+                    if (rc != GSI_OK) return rc;
+                    t_best = std::min(t_best, std::chrono::duration<double, std::milli>(t1 - t0).count());
                 }
-                bo.seeds_per_item = c;
-                std::vector<gsi_result *> res;
-                std::vector<gsi_status> sts;
-                auto t0 = std::chrono::steady_clock::now();
-                gsi_status rc = batch_execute(g, plans, bo, res, sts);
-                if (bo.stream) cudaStreamSynchronize((cudaStream_t)bo.stream);
-                auto t1 = std::chrono::steady_clock::now();
-                for (gsi_result *r : res) delete r;
-                if (rc != GSI_OK) return rc;
-                t_best = std::min(t_best, std::chrono::duration<double, std::milli>(t1 - t0).count());
-            }
-            if (t_best < best) {
-                best = t_best;
-                arg = c;
+                if (t_best < best) {
+                    best = t_best;
+                    arg_spi = spi;
+                    arg_rows = rows;
+                }
             }
         }
-        if (best_seeds_per_item) *best_seeds_per_item = arg;
+        if (best_seeds_per_item) *best_seeds_per_item = arg_spi;
+        if (best_item_rows) *best_item_rows = arg_rows;
         if (best_ms) *best_ms = best;
         return GSI_OK;
     } catch (const std::bad_alloc &) {
@@ -275,7 +309,7 @@ static void server_worker(gsi_server *s, int idx) {
     cudaStream_t st = s->streams[idx];
     const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
     const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
-    const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 8;
+    const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 16;
     // the slot's batch workspace, allocated once (results are gathered out)
     BatchWorkspace ws;
     if (max_batch > 1) {

@@ -26,7 +26,7 @@ EXPORTED = [
     "gsi_graph_create", "gsi_graph_destroy", "gsi_graph_get_info", "gsi_graph_export", "gsi_graph_label_freq",
     "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_destroy",
     "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_join_step_noalloc", "gsi_plan_order",
-    "gsi_batch_run", "gsi_batch_autotune", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
+    "gsi_batch_run", "gsi_batch_autotune", "gsi_batch_prepare", "gsi_batch_replay", "gsi_batch_destroy", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
     "gsi_server_destroy", "gsi_last_error", "gsi_version", "gsi_selftest_wait_timeout",
 ]
 
@@ -150,8 +150,15 @@ def load(build_if_missing: bool = False):
                                 ctypes.POINTER(VP), I32P]
     L.gsi_batch_run.restype = st
     L.gsi_batch_autotune.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
-                                     I32P, ctypes.POINTER(ctypes.c_double)]
+                                     I32P, I32P, ctypes.POINTER(ctypes.c_double)]
     L.gsi_batch_autotune.restype = st
+    L.gsi_batch_prepare.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
+                                    ctypes.POINTER(VP), I32P]
+    L.gsi_batch_prepare.restype = st
+    L.gsi_batch_replay.argtypes = [VP, ctypes.POINTER(VP), I32P, ctypes.POINTER(c_stats)]
+    L.gsi_batch_replay.restype = st
+    L.gsi_batch_destroy.argtypes = [VP]
+    L.gsi_batch_destroy.restype = None
     L.gsi_server_create.argtypes = [VP, ctypes.POINTER(c_server_opts), ctypes.POINTER(VP)]
     L.gsi_server_create.restype = st
     L.gsi_server_submit.argtypes = [VP, ctypes.POINTER(c_query_desc), U64P]
@@ -382,16 +389,54 @@ class Graph:
         return res
 
 
-def batch_autotune(graph: "Graph", queries, stream=None, mem_budget: int = 0) -> tuple[int, float]:
-    """Pick the batch work-item size on a calibration batch: (seeds_per_item, ms)."""
+class PreparedBatch:
+    """A batch planned once and replayed from a captured CUDA graph (gsi_batch_prepare / gsi_batch_replay)."""
+
+    def __init__(self, graph: "Graph", queries, stream=None, row_cap: int = 0, mem_budget: int = 0,
+                 count_only: bool = False, seeds_per_item: int = 0, item_rows: int = 0, counters: bool = False):
+        self._graph = graph
+        self._qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
+        self._descs = (c_query_desc * len(self._qas))(*[qa.desc() for qa in self._qas])
+        self.statuses = (ctypes.c_int32 * len(self._qas))()
+        self._probe = c_stats() if counters else None
+        o = c_batch_opts(_stream_handle(stream), row_cap, mem_budget, int(count_only),
+                         ctypes.pointer(self._probe) if counters else None, seeds_per_item, item_rows)
+        h = VP()
+        _check(load().gsi_batch_prepare(graph.handle, self._descs, len(self._qas), ctypes.byref(o), ctypes.byref(h),
+                                        self.statuses), "gsi_batch_prepare")
+        self._h = h.value
+
+    def __len__(self):
+        return len(self._qas)
+
+    def run(self, stats: c_stats | None = None) -> list:
+        n = len(self._qas)
+        outs = (VP * n)()
+        sts = (ctypes.c_int32 * n)()
+        _check(load().gsi_batch_replay(self._h, outs, sts, ctypes.pointer(stats) if stats is not None else None),
+               "gsi_batch_replay")
+        return [Result(outs[i]) if sts[i] == GSI_OK else GsiError(sts[i], "batched query failed") for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gsi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def batch_autotune(graph: "Graph", queries, stream=None, mem_budget: int = 0) -> tuple[int, int, float]:
+    """Pick the batch work-unit sizes on a calibration batch: (seeds_per_item, item_rows, ms)."""
     qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
     descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
     o = c_batch_opts(_stream_handle(stream), 0, mem_budget, 0, None, 0, 0)
-    best = ctypes.c_int32()
+    spi = ctypes.c_int32()
+    rows = ctypes.c_int32()
     ms = ctypes.c_double()
-    _check(load().gsi_batch_autotune(graph.handle, descs, len(qas), ctypes.byref(o), ctypes.byref(best),
-                                     ctypes.byref(ms)), "gsi_batch_autotune")
-    return int(best.value), float(ms.value)
+    _check(load().gsi_batch_autotune(graph.handle, descs, len(qas), ctypes.byref(o), ctypes.byref(spi),
+                                     ctypes.byref(rows), ctypes.byref(ms)), "gsi_batch_autotune")
+    return int(spi.value), int(rows.value), float(ms.value)
 
 
 def query_signatures(q) -> np.ndarray:

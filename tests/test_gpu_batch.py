@@ -122,8 +122,8 @@ def test_batch_results_outlive_each_other(pkg, world):
 def test_batch_autotune_and_item_sizes(pkg, world):
     """The autotuner returns one of its candidate sizes; every item size gives the same results."""
     g, G, O, qs = world
-    best, ms = pkg.batch_autotune(G, qs[:16])
-    assert best in (16, 32, 64, 128, 256) and ms > 0
+    best, rows, ms = pkg.batch_autotune(G, qs[:16])
+    assert best in (32, 64, 128) and rows in (512, 1024, 2048) and ms > 0
     ref = [oracle.count(O, q)[0] for q in qs[:16]]
     for spi in (1, 7, 32, 4096):
         res = G.batch(qs[:16], seeds_per_item=spi)
@@ -139,3 +139,62 @@ def test_batch_autotune_and_item_sizes(pkg, world):
             assert np.array_equal(oracle.sort_rows(r.rows()), oracle.sort_rows(G.query(q).rows()))
         units[ir] = st.tiles
     assert units[7] > units[-1] and units[64] > units[-1]
+
+
+def test_batch_filter_many_query_vertices(pkg, world):
+    """A batch with more query vertices than the filter's shared-memory
+    counters hold (> 24,576) counts through global atomics; counts and sets
+    still match the plain path on a sample."""
+    g, G, O, qs = world
+    big = [qs[i % len(qs)] for i in range(6200)]          # about 31,000 query vertices
+    assert sum(len(np.asarray(q.vlab)) for q in big) > 24576
+    res = G.batch(big, count_only=True)
+    ref = [G.query(q, count_only=True).count for q in qs]
+    for i in range(0, len(big), 97):
+        assert res[i].count == ref[i % len(qs)]
+
+
+def test_prepared_batch_replays(pkg, world):
+    """A prepared batch replayed from its captured graph gives the oracle's
+    sets on every replay; results outlive later replays and the batch."""
+    import torch
+    g, G, O, qs = world
+    want = [oracle.enumerate_rows(O, q) for q in qs[:24]]
+    s = torch.cuda.Stream()
+    for stream in (None, s):
+        pb = pkg.PreparedBatch(G, qs[:24], stream=stream, counters=True)
+        assert list(pb.statuses) == [0] * 24
+        first = pb.run()
+        for _ in range(2):
+            st = pkg.c_stats()
+            again = pb.run(stats=st)
+            assert st.join_launches == 1 and st.filter_launches == 1 and st.join_bytes > 0
+            for r, w in zip(again, want):
+                assert np.array_equal(oracle.sort_rows(r.rows()), w)
+        pb.close()
+        for r, w in zip(first, want):                      # still valid
+            assert r.count == w.shape[0]
+            assert np.array_equal(oracle.sort_rows(r.rows()), w)
+
+
+def test_prepared_batch_statuses_caps_and_small_budget(pkg, world):
+    g, G, O, qs = world
+    bad = H.query(3, [(0, 1)])                               # disconnected
+    mix = [qs[0], bad, qs[1]]
+    pb = pkg.PreparedBatch(G, mix)
+    assert list(pb.statuses) == [0, pkg.GSI_EINVAL, 0]
+    res = pb.run()
+    assert isinstance(res[1], pkg.GsiError) and res[1].status == pkg.GSI_EINVAL
+    assert res[0].count == oracle.count(O, qs[0])[0] and res[2].count == oracle.count(O, qs[2 - 1])[0]
+    pb.close()
+    ref = [oracle.count(O, q)[0] for q in qs[:12]]
+    pb = pkg.PreparedBatch(G, qs[:12], count_only=True)
+    assert [r.count for r in pb.run()] == ref
+    pb.close()
+    pb = pkg.PreparedBatch(G, qs[:12], row_cap=5)
+    for r, c in zip(pb.run(), ref):
+        assert r.count == c and r.rows().shape[0] == min(5, c)
+    pb.close()
+    pb = pkg.PreparedBatch(G, qs[:12], mem_budget=1 << 20)  # no slice fits: every query on the plain path
+    assert [r.count for r in pb.run()] == ref
+    pb.close()
