@@ -138,25 +138,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {"k_query": ("join.cu", "join_tile.cuh", "common.cuh", "scan.cuh", "internal.h"),
+                  "k_batch": ("batch.cu", "join_tile.cuh", "common.cuh", "internal.h")}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("join.cu", "common.cuh", "scan.cuh", "internal.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1906_03420_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """ncu DRAM bytes per k_join launch recorded under profiles/, if taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"k_join_{workload}_traffic.json")
+def recorded_traffic(kernel: str, workload: str, alg_bytes_per_launch):
+    """DRAM bytes per launch of `kernel` from the ncu record under profiles/
+    (only if taken on the current kernel source): measured on this workload,
+    or scaled from a smaller capture by algorithmic bytes.  (bytes, source)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
-        return None
-    if rec.get("kernel_source_sha") != kernel_source_hash():
-        return None
-    return rec.get("dram_bytes_per_launch")
+        return None, None
+    if rec.get("kernel_source_sha") != kernel_source_hash(kernel):
+        return None, None
+    if rec.get("dram_bytes_per_launch") is not None and rec.get("same_workload"):
+        return rec["dram_bytes_per_launch"], rec.get("source")
+    if rec.get("ratio_to_alg_bytes") is not None and alg_bytes_per_launch:
+        return rec["ratio_to_alg_bytes"] * alg_bytes_per_launch, rec.get("source")
+    return None, None
 
 
 # --------------------------------------------------------------------- GPU arm
@@ -327,11 +337,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     hbm_peak = peaks.get("hbm_gbs")
     jb, jms, jl = float(allv[:, 4].sum()), float(allv[:, 3].sum()), float(allv[:, 5].sum())
     achieved = (jb / jl) / ((jms / jl) * 1e-3) / 1e9 if jl > 0 and jms > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_join", "achieved": achieved,
+    kname = "k_batch" if batched else "k_query"
+    traffic, traffic_src = recorded_traffic(kname, args.workload, jb / jl if jl else None)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
                 "peak": hbm_peak if hbm_peak else 6800.0, "unit": "GB/s",
                 "peak_source": "measured" if hbm_peak else "fallback",
                 "frac": (achieved / (hbm_peak or 6800.0)) if achieved else None,
-                "traffic": recorded_traffic(args.workload),
+                "traffic": traffic, "traffic_source": traffic_src,
                 "alg_bytes_per_launch": jb / jl if jl else None, "launches": int(jl),
                 "avg_launch_us": jms / jl * 1e3 if jl else None,
                 "share_of_device_time": jms / (t_max_ms * world) if t_max_ms else None}

@@ -136,7 +136,7 @@ struct QueryCtl {
     unsigned pad;
     unsigned long long spin_limit;   // sleeps before a barrier wait gives up (0 = default)
 };
-constexpr int QUERY_MAX_CTAS = 1024;
+constexpr int QUERY_MAX_CTAS = 2048;
 size_t join_args_size();
 // Self-test of the bounded grid barrier: a cooperative launch whose barrier
 // expects one CTA more than it has, so every wait must run out.  Returns

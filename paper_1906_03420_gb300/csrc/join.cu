@@ -419,7 +419,7 @@ gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &st
         set_error("join: the query kernel does not fit on an SM");
         return GSI_EINVAL;
     }
-    if (per_sm > 4) per_sm = 4;
+    if (per_sm > 1024 / JOIN_NT) per_sm = 1024 / JOIN_NT;     // at most 32 warps per SM
     int grid = (dev >= 0 && dev < 64 ? nsm[dev] : 152) * per_sm;
     if (grid > QUERY_MAX_CTAS) grid = QUERY_MAX_CTAS;
     *grid_out = grid;
