@@ -205,17 +205,34 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
             if ((R + 1) * 8 + 64 > S_words * 8) { failed = true; break; }
             uint64_t *F = S;
             // bounds and slot offsets (CTA-local scan)
-            unsigned long long run = 0;
+            unsigned long long run = 0, abytes = 0;
             for (uint64_t base = 0; base < R; base += BNT) {
                 const uint64_t i = base + threadIdx.x;
                 unsigned long long v = 0;
-                if (i < R) v = (unsigned long long)row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl) + W;
+                if (i < R) {
+                    uint32_t c;
+                    if (a.stats) {
+                        uint64_t lsum;
+                        c = row_bound_sum(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lsum);
+                        abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
+                    } else {
+                        c = row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl);
+                    }
+                    v = (unsigned long long)c + W;
+                }
                 unsigned long long tot;
                 const unsigned long long ex = block_exclusive_scan<BNT, unsigned long long>(v, wt, &tot) + run;
                 if (i < R) F[i] = ex;
                 run += tot;
             }
             const uint64_t total = run;
+            if (a.stats) {                       // one add per step of a unit
+                abytes = block_sum<BNT, unsigned long long>(abytes, wt);
+                if (threadIdx.x == 0) {
+                    if (abytes) atomicAdd(a.stats, abytes);
+                    atomicAdd(a.stats + 1, (unsigned long long)(total - W * R));
+                }
+            }
             if (threadIdx.x == 0) {
                 F[R] = total;
                 cnt_s = 0;
@@ -235,11 +252,13 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
                 for (uint64_t j = threadIdx.x; j <= lim; j += BNT) cn += F[r_lo + j] <= s_next;
                 cn = block_sum<BNT, unsigned long long>(cn, wt);
                 const int64_t r_next = r_lo + (int64_t)cn - 1;
-                join_tile<BNT, BVT>(a, M, (int64_t)R, F, total, r_lo, r_next, out, cap, &cnt_s, tile);
+                join_tile<BNT, BVT, false>(a, M, (int64_t)R, F, total, r_lo, r_next, out, cap, &cnt_s, tile);
                 r_lo = r_next;
             }
             __syncthreads();
             const uint64_t cnt = cnt_s;
+            if (a.stats && threadIdx.x == 0)     // survivors written
+                atomicAdd(a.stats, 4ull * (uint64_t)(t + 1) * min(cnt, cap));
             if (!last && cnt > cap) { failed = true; break; }
             M = out;
             oreg ^= 1;

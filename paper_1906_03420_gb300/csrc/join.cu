@@ -218,14 +218,25 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
         const uint64_t per = (R + G - 1) / G;
         const uint64_t chunk = (per + SCAN_NV - 1) / SCAN_NV * SCAN_NV;
         const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(R, lo + chunk);
-        unsigned long long sum = 0, sbytes = 0;
+        unsigned long long sum = 0, abytes = 0;
         for (uint64_t i = lo + threadIdx.x; i < hi; i += NT) {
-            uint32_t c = row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl);
+            uint32_t c;
+            if (a.stats) {
+                uint64_t lsum;
+                c = row_bound_sum(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lsum);
+                abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
+            } else {
+                c = row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl);
+            }
             caps[i] = c;
             sum += (unsigned long long)c + W;
         }
         sum = block_sum<NT, unsigned long long>(sum, wt);
         if (threadIdx.x == 0) bsum[blockIdx.x] = sum;
+        if (a.stats) {                       // one add per CTA and step
+            abytes = block_sum<NT, unsigned long long>(abytes, wt);
+            if (threadIdx.x == 0 && abytes) atomicAdd(a.stats, abytes);
+        }
         if (!grid_barrier(ctl, G)) return;
         // phase 2: slot offsets F (each CTA rescans its own chunk)
         cta_prefix(bsum, G, wt, &pre, &tot);
@@ -256,7 +267,7 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             st->total = total;
             st->ntiles = ntiles;
             st->out_cap = cap;
-            if (a.stats) atomicAdd(a.stats, (unsigned long long)R * (4ull * a.s.d + 8ull * a.s.d + 8ull));
+            if (a.stats) atomicAdd(a.stats + 1, (unsigned long long)(total - W * R));   // candidate slots
         }
         if (!grid_barrier(ctl, G)) return;
         // phase 3: first row of every tile
@@ -277,10 +288,12 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             __syncthreads();
             const uint64_t tile = tile_s;
             if (tile >= ntiles) break;
-            join_tile<NT, VT>(a, M, (int64_t)R, F, total, __ldcg(part + tile), __ldcg(part + tile + 1), st->out, cap,
-                              &st->count, tile);
+            join_tile<NT, VT, false>(a, M, (int64_t)R, F, total, __ldcg(part + tile), __ldcg(part + tile + 1), st->out,
+                                     cap, &st->count, tile);
         }
         if (!grid_barrier(ctl, G)) return;
+        if (a.stats && blockIdx.x == 0 && threadIdx.x == 0)        // survivors written
+            atomicAdd(a.stats, 4ull * (uint64_t)(t + 1) * min((uint64_t)__ldcg(&st->count), cap));
     }
 }
 

@@ -50,6 +50,32 @@ __device__ inline uint32_t row_bound(const StepDev &s, const int32_t *row, const
     return best;
 }
 
+// row_bound plus the summed length of the row's label sub-lists (for the
+// algorithmic-byte count).
+__device__ inline uint32_t row_bound_sum(const StepDev &s, const int32_t *row, const uint32_t *__restrict__ off,
+                                         const uint16_t *__restrict__ cl, uint64_t *lsum) {
+    uint32_t best = 0xffffffffu;
+    uint64_t sum = 0;
+    for (int j = 0; j < s.d; ++j) {
+        uint64_t seg = (uint64_t)(uint32_t)__ldcg(row + s.col[j]) * (uint64_t)s.L + (uint64_t)s.lab[j];
+        uint32_t a = __ldg(off + seg), b = __ldg(off + seg + 1), lo, hi;
+        label_range(cl, a, b, (uint32_t)s.ulab, &lo, &hi);
+        best = min(best, hi - lo);
+        sum += hi - lo;
+    }
+    *lsum = sum;
+    return best;
+}
+
+// Algorithmic bytes of one row of a join step (t columns, d linking lists,
+// label sub-lists summing to lsum, the shortest of length best): read the
+// row, locate each list and its label sub-range, read the other sub-lists,
+// and one list element plus one bitmap word per candidate slot.  Survivors
+// add 4(t+1) each when written.
+__device__ __forceinline__ unsigned long long row_alg_bytes(int t, int d, uint64_t lsum, uint32_t best) {
+    return 4ull * t + 16ull * d + 4ull * (lsum - best) + 8ull * best;
+}
+
 struct JoinArgs {
     const int32_t *M;
     int64_t R;
@@ -102,7 +128,7 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
 // one persistent launch (ping-pong table regions, one scratch region for
 // every step), so they are read through L2 (ld.global.cg) and never through
 // the non-coherent read-only path.
-template <int NT, int VT>
+template <int NT, int VT, bool TILE_STATS = true>
 __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, int64_t R,
                                           const uint64_t *F, uint64_t total, int64_t r_lo,
                                           int64_t r_next, int32_t *__restrict__ out, uint64_t out_cap,
@@ -161,7 +187,7 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         }
         const uint64_t fr = Fs[lr];
         if (fr > s0 && fr < s1) rowmap[fr - s0] = (uint16_t)lr;       // first slot of the row in this tile
-        if (a.stats && fr >= s0) bytes += 4ull * t + 8ull * d + 4ull * (lsum - best);   // row owned by this tile
+        if (TILE_STATS && a.stats && fr >= s0) bytes += 4ull * t + 8ull * d + 4ull * (lsum - best);   // row owned by this tile
     }
     __syncthreads();
     {   // slot -> row: inclusive max-scan of the row-start marks
@@ -260,7 +286,7 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
             if (colx >= W1) { colx -= W1; ++row; }
         }
     }
-    if (a.stats) {
+    if (TILE_STATS && a.stats) {
         bytes += 8ull * items;                                    // list element + bitmap probe
         if (!a.count_only && threadIdx.x == 0) bytes += 4ull * (t + 1) * nsurv;
         unsigned long long bsum = block_sum<NT, unsigned long long>(bytes, wt);
