@@ -152,7 +152,7 @@ typedef struct {
  * Alg. 2, then one join iteration per remaining query vertex (Alg. 3 with the
  * Alg. 4 upper bound on each row's output).  The steps run device-driven in
  * an arena (one scratch and two table regions, sizes kept on the device, no
- * host wait between steps) of min(mem_budget, 8 GiB) bytes; if a table does
+ * host wait between steps) of min(mem_budget, 16 GiB) bytes; if a table does
  * not fit, the query is redone with an arena four times larger, up to
  * mem_budget, and past that host-driven, with row ranges halved until each
  * fits.  (A single arena of the whole default budget costs milliseconds per

@@ -202,22 +202,25 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
         for (int t = t0; t < k && R > 0 && !skip; ++t) {
             const JoinArgs &a = b.cfgs[bq->cfg0 + t];
             int32_t *out = reg[oreg];
-            if ((R + 1) * 8 + 64 > S_words * 8) { failed = true; break; }
+            if ((R + 1) * 8 + R * 8 + 64 > S_words * 8) { failed = true; break; }
             uint64_t *F = S;
+            uint32_t *bnd = reinterpret_cast<uint32_t *>(S + S_words) - R;   // bound records (see join_tile)
+            uint32_t *blo = bnd - R;
             // bounds and slot offsets (CTA-local scan)
             unsigned long long run = 0, abytes = 0;
+            bool too_long = false;
             for (uint64_t base = 0; base < R; base += BNT) {
                 const uint64_t i = base + threadIdx.x;
                 unsigned long long v = 0;
                 if (i < R) {
-                    uint32_t c;
-                    if (a.stats) {
-                        uint64_t lsum;
-                        c = row_bound_sum(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lsum);
-                        abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
-                    } else {
-                        c = row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl);
-                    }
+                    uint32_t lob;
+                    int jb;
+                    uint64_t lsum;
+                    const uint32_t c = row_bound_full(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lob, &jb, &lsum);
+                    if (a.stats) abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
+                    too_long |= c > BOUND_LEN_MASK;
+                    bnd[i] = (c & BOUND_LEN_MASK) | ((uint32_t)jb << BOUND_LEN_BITS);
+                    blo[i] = lob;
                     v = (unsigned long long)c + W;
                 }
                 unsigned long long tot;
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
                 run += tot;
             }
             const uint64_t total = run;
+            if (__syncthreads_or(too_long)) { failed = true; break; }   // record too small: the plain path
             if (a.stats) {                       // one add per step of a unit
                 abytes = block_sum<BNT, unsigned long long>(abytes, wt);
                 if (threadIdx.x == 0) {
@@ -252,7 +256,8 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
                 for (uint64_t j = threadIdx.x; j <= lim; j += BNT) cn += F[r_lo + j] <= s_next;
                 cn = block_sum<BNT, unsigned long long>(cn, wt);
                 const int64_t r_next = r_lo + (int64_t)cn - 1;
-                join_tile<BNT, BVT, false>(a, M, (int64_t)R, F, total, r_lo, r_next, out, cap, &cnt_s, tile);
+                join_tile<BNT, BVT, false, true>(a, M, (int64_t)R, F, total, r_lo, r_next, out, cap, &cnt_s, tile,
+                                                 bnd, blo);
                 r_lo = r_next;
             }
             __syncthreads();

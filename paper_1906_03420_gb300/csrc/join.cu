@@ -207,30 +207,34 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 2u);
             return;
         }
-        if ((R + 1) * 8 + R * 4 + 64 > st->S_words * 8) {
+        if ((R + 1) * 8 + R * 8 + 64 > st->S_words * 8) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
             return;
         }
         uint64_t *F = st->S;
+        // per-row bound records at the end of the scratch region: length and
+        // linking-edge index of the shortest sub-list, and its start
         uint32_t *caps = reinterpret_cast<uint32_t *>(st->S + st->S_words) - R;
+        uint32_t *blo = caps - R;
         const int32_t *M = st->M;
         // phase 1: each row's bound (the shortest label sub-list), per-CTA sums
         const uint64_t per = (R + G - 1) / G;
         const uint64_t chunk = (per + SCAN_NV - 1) / SCAN_NV * SCAN_NV;
         const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(R, lo + chunk);
         unsigned long long sum = 0, abytes = 0;
+        bool too_long = false;
         for (uint64_t i = lo + threadIdx.x; i < hi; i += NT) {
-            uint32_t c;
-            if (a.stats) {
-                uint64_t lsum;
-                c = row_bound_sum(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lsum);
-                abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
-            } else {
-                c = row_bound(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl);
-            }
-            caps[i] = c;
+            uint32_t lob;
+            int jb;
+            uint64_t lsum;
+            const uint32_t c = row_bound_full(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lob, &jb, &lsum);
+            if (a.stats) abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
+            too_long |= c > BOUND_LEN_MASK;
+            caps[i] = (c & BOUND_LEN_MASK) | ((uint32_t)jb << BOUND_LEN_BITS);
+            blo[i] = lob;
             sum += (unsigned long long)c + W;
         }
+        if (too_long) atomicOr(&ctl->fail, 1u);    // a sub-list too long for the record: splitting path
         sum = block_sum<NT, unsigned long long>(sum, wt);
         if (threadIdx.x == 0) bsum[blockIdx.x] = sum;
         if (a.stats) {                       // one add per CTA and step
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
         uint64_t cap = st->out_bytes / (4ull * (uint64_t)(t + 1));
         if (st->row_cap && st->row_cap < cap) cap = st->row_cap;
         if (st->count_only) cap = 0;
-        if ((R + 1 + ntiles + 1) * 8 + R * 4 + 64 > st->S_words * 8) {
+        if ((R + 1 + ntiles + 1) * 8 + R * 8 + 64 > st->S_words * 8) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
             return;
         }
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             unsigned long long run = pre;
             for (uint64_t base = lo; base < hi; base += NT) {
                 const uint64_t i = base + threadIdx.x;
-                const unsigned long long v = i < hi ? (unsigned long long)caps[i] + W : 0ull;
+                const unsigned long long v = i < hi ? (unsigned long long)(caps[i] & BOUND_LEN_MASK) + W : 0ull;
                 unsigned long long t2;
                 const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(v, wt, &t2) + run;
                 if (i < hi) F[i] = ex;
@@ -288,8 +292,8 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
             __syncthreads();
             const uint64_t tile = tile_s;
             if (tile >= ntiles) break;
-            join_tile<NT, VT, false>(a, M, (int64_t)R, F, total, __ldcg(part + tile), __ldcg(part + tile + 1), st->out,
-                                     cap, &st->count, tile);
+            join_tile<NT, VT, false, true>(a, M, (int64_t)R, F, total, __ldcg(part + tile), __ldcg(part + tile + 1),
+                                           st->out, cap, &st->count, tile, caps, blo);
         }
         if (!grid_barrier(ctl, G)) return;
         if (a.stats && blockIdx.x == 0 && threadIdx.x == 0)        // survivors written

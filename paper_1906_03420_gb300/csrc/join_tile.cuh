@@ -67,6 +67,52 @@ __device__ inline uint32_t row_bound_sum(const StepDev &s, const int32_t *row, c
     return best;
 }
 
+// Bits of a per-row bound record: the shortest sub-list's length in the low
+// 27 bits, the index of its linking edge above (lists stay below 2^27).
+constexpr uint32_t BOUND_LEN_BITS = 27;
+constexpr uint32_t BOUND_LEN_MASK = (1u << BOUND_LEN_BITS) - 1;
+
+// row_bound plus where the shortest sub-list starts and which linking edge
+// gives it (the join tile then stages the row without searching again), and
+// the summed length of all sub-lists.
+__device__ inline uint32_t row_bound_full(const StepDev &s, const int32_t *row, const uint32_t *__restrict__ off,
+                                          const uint16_t *__restrict__ cl, uint32_t *lo_best, int *jb,
+                                          uint64_t *lsum) {
+    uint32_t best = 0xffffffffu, bl = 0;
+    int bj = 0;
+    uint64_t sum = 0;
+    for (int j = 0; j < s.d; ++j) {
+        uint64_t seg = (uint64_t)(uint32_t)__ldcg(row + s.col[j]) * (uint64_t)s.L + (uint64_t)s.lab[j];
+        uint32_t a = __ldg(off + seg), b = __ldg(off + seg + 1), lo, hi;
+        label_range(cl, a, b, (uint32_t)s.ulab, &lo, &hi);
+        if (hi - lo < best) {
+            best = hi - lo;
+            bl = lo;
+            bj = j;
+        }
+        sum += hi - lo;
+    }
+    *lo_best = bl;
+    *jb = bj;
+    *lsum = sum;
+    return best;
+}
+
+// Membership of x (label rank r) in a whole list ci[a..b), sorted by
+// (label rank, id): binary search on the pair.
+__device__ inline bool ranked_contains(const int32_t *__restrict__ ci, const uint16_t *__restrict__ cl, uint32_t a,
+                                       uint32_t b, uint32_t r, int32_t x) {
+    uint32_t lo = a, hi = b;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t cm = __ldg(cl + mid);
+        const bool less = cm < r || (cm == r && __ldg(ci + mid) < x);
+        if (less) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < b && __ldg(cl + lo) == r && __ldg(ci + lo) == x;
+}
+
 // Algorithmic bytes of one row of a join step (t columns, d linking lists,
 // label sub-lists summing to lsum, the shortest of length best): read the
 // row, locate each list and its label sub-range, read the other sub-lists,
@@ -128,11 +174,17 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
 // one persistent launch (ping-pong table regions, one scratch region for
 // every step), so they are read through L2 (ld.global.cg) and never through
 // the non-coherent read-only path.
-template <int NT, int VT, bool TILE_STATS = true>
+//
+// With bounds (PRE), the bound scan already found each row's shortest label
+// sub-list: bnd[r] holds its length and linking-edge index (BOUND_LEN_BITS),
+// blo[r] its start.  Staging then reads those instead of searching, and the
+// other linking lists are probed whole with the (label rank, id) key.
+template <int NT, int VT, bool TILE_STATS = true, bool PRE = false>
 __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, int64_t R,
                                           const uint64_t *F, uint64_t total, int64_t r_lo,
                                           int64_t r_next, int32_t *__restrict__ out, uint64_t out_cap,
-                                          unsigned long long *out_count, uint64_t tile) {
+                                          unsigned long long *out_count, uint64_t tile,
+                                          const uint32_t *bnd = nullptr, const uint32_t *blo = nullptr) {
     constexpr int NV = NT * VT;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long wt[NT / 32];
@@ -163,6 +215,26 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         const int32_t *row = M + (r_lo + lr) * (int64_t)t;
         int32_t *rv = rowv + lr * t;
         for (int c = 0; c < t; ++c) rv[c] = __ldcg(row + c);
+        if (PRE) {
+            // the bound scan's record: candidates from the shortest sub-list,
+            // every other linking list taken whole
+            const uint32_t bw = __ldcg(bnd + r_lo + lr);
+            const uint32_t best = bw & BOUND_LEN_MASK;
+            const int jb = (int)(bw >> BOUND_LEN_BITS);
+            base0[lr] = __ldcg(blo + r_lo + lr);
+            int q = 0;
+            for (int j = 0; j < d && best > 0; ++j) {
+                if (j == jb) continue;
+                const uint64_t seg = (uint64_t)(uint32_t)rv[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+                const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
+                lst[(lr * dm1 + q) * 2] = x0;
+                lst[(lr * dm1 + q) * 2 + 1] = x1 - x0;
+                ++q;
+            }
+            const uint64_t fr = Fs[lr];
+            if (fr > s0 && fr < s1) rowmap[fr - s0] = (uint16_t)lr;
+            continue;
+        }
         // the row's lists: the shortest label sub-list supplies candidates
         uint32_t lo[GSI_MAX_QUERY_VERTICES], len[GSI_MAX_QUERY_VERTICES];
         uint32_t best = 0xffffffffu;
@@ -235,7 +307,8 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         for (int c = 0; c < t && ok; ++c) ok = rv[c] != w;
         for (int j = 0; j < dm1 && ok; ++j) {
             const uint32_t *ls = lst + (lr * dm1 + j) * 2;
-            ok = sorted_contains(a.ci + ls[0], ls[1], w);
+            if (PRE) ok = ranked_contains(a.ci, a.cl, ls[0], ls[0] + ls[1], (uint32_t)a.s.ulab, w);
+            else ok = sorted_contains(a.ci + ls[0], ls[1], w);
         }
         wv[k] = w;
         lrv[k] = lr;

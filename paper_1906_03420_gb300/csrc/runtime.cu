@@ -232,7 +232,7 @@ void Timer::resolve(gsi_stats *s) {
 // First device-driven arena of a query.  Reserving an arena near the whole
 // default budget (a large share of HBM) from the stream-ordered pool costs
 // milliseconds per query; arenas up to tens of GB cost well under one.
-constexpr uint64_t DEVICE_ARENA_START = 8ull << 30;
+constexpr uint64_t DEVICE_ARENA_START = 16ull << 30;
 
 static gsi_status dalloc(Exec &x, void **p, uint64_t bytes) {
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, x.st);
@@ -378,7 +378,10 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     *no_memory = false;
     const uint64_t B = arena_bytes;
     const uint64_t align = 256;
-    const uint64_t s_bytes = (B / 5) / align * align;
+    // a third each: scratch (16 bytes per input row: offsets and bound
+    // records) and two table regions (a row of t + 1 >= 4 columns needs as
+    // much table space as its successor step needs scratch)
+    const uint64_t s_bytes = (B / 3) / align * align;
     const uint64_t t_bytes = ((B - s_bytes) / 2) / align * align;
     if (s_bytes < (1 << 16) || t_bytes < (uint64_t)g->n * 4 + 1024) {
         *overflow = true;
@@ -471,6 +474,13 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
         return rc;
     }
     const uint64_t count = fin[1];
+    // the last table must hold every row asked for (all, or up to the row cap)
+    const uint64_t need = count_only ? 0 : (row_cap ? std::min(count, row_cap) : count);
+    if (need > fin[2]) {
+        release();
+        *overflow = true;
+        return GSI_OK;
+    }
     const uint64_t rows = std::min(count, fin[2]);
     int32_t *final_reg = reg[(k - 1) & 1];
     res->count += count;
@@ -629,7 +639,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         // device-driven path first; the host-driven splitting path on overflow
         bool overflow = true;
         if (!o.host_driven && q.k > 1) {
-            // arenas of 8 GiB, then x4 per overflow, up to the budget
+            // arenas of 16 GiB, then x4 per overflow, up to the budget
             uint64_t arena = std::min<uint64_t>(x.budget, DEVICE_ARENA_START);
             for (;;) {
                 bool no_memory = false;
