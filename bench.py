@@ -432,6 +432,8 @@ def run_served(args) -> dict:
     def open_loop(kind, rate):
         arrivals = synth.poisson_arrivals(3000, nq, rate)
         S = make(kind)
+        for q in queries[: min(32, nq)]:                     # warm-up: pools and caches settle first
+            S.poll(S.submit(q), -1)[0].close()
         tickets = [None] * nq
         lat = np.zeros(nq)
         emb = [0]

@@ -296,6 +296,7 @@ struct gsi_server {
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    std::vector<BatchWorkspace> ws;        // one per slot (empty when batching is off)
 };
 
 // One slot: a worker thread with its own stream and an equal share of the
@@ -310,24 +311,10 @@ static void server_worker(gsi_server *s, int idx) {
     const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
     const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
     const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 16;
-    // the slot's batch workspace, allocated once (results are gathered out)
-    BatchWorkspace ws;
-    if (max_batch > 1) {
-        ws.result_bytes = (share / 5) / 256 * 256;
-        ws.arena_bytes = (share - ws.result_bytes) / 256 * 256;
-        if (cudaMalloc(&ws.arena, ws.arena_bytes) != cudaSuccess || cudaMalloc(&ws.result, ws.result_bytes) != cudaSuccess) {
-            if (ws.arena) cudaFree(ws.arena);
-            ws = BatchWorkspace();
-            (void)cudaGetLastError();
-        }
-    }
-    struct WsGuard {
-        BatchWorkspace &w;
-        ~WsGuard() {
-            if (w.arena) cudaFree(w.arena);
-            if (w.result) cudaFree(w.result);
-        }
-    } wsg{ws};
+    (void)share;
+    // the slot's batch workspace, reserved by gsi_server_create (results are
+    // gathered out of it, so it is reused at once)
+    BatchWorkspace &ws = s->ws[idx];
     for (;;) {
         std::vector<std::shared_ptr<gsi_server::Req>> batch;
         {
@@ -421,6 +408,21 @@ extern "C" gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opt
         GSI_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         s->streams.push_back(st);
     }
+    // each slot's batch workspace, reserved here so that no request waits for it
+    s->ws.assign((size_t)s->opts.n_streams, BatchWorkspace());
+    if (s->opts.max_batch != 1) {
+        const uint64_t share = s->opts.mem_budget / (uint64_t)s->opts.n_streams;
+        for (BatchWorkspace &w : s->ws) {
+            w.result_bytes = (share / 5) / 256 * 256;
+            w.arena_bytes = (share - w.result_bytes) / 256 * 256;
+            if (cudaMalloc(&w.arena, w.arena_bytes) != cudaSuccess ||
+                cudaMalloc(&w.result, w.result_bytes) != cudaSuccess) {
+                if (w.arena) cudaFree(w.arena);           // batches then reserve their own memory
+                w = BatchWorkspace();
+                (void)cudaGetLastError();
+            }
+        }
+    }
     for (int i = 0; i < s->opts.n_streams; ++i) s->workers.emplace_back(server_worker, s.get(), i);
     *out = s.release();
     return GSI_OK;
@@ -499,5 +501,9 @@ extern "C" void gsi_server_destroy(gsi_server *s) {
     for (auto &kv : s->all)
         if (kv.second->res) gsi_result_destroy(kv.second->res);
     for (auto st : s->streams) cudaStreamDestroy(st);
+    for (BatchWorkspace &w : s->ws) {
+        if (w.arena) cudaFree(w.arena);
+        if (w.result) cudaFree(w.result);
+    }
     delete s;
 }
