@@ -54,6 +54,10 @@ def _load():
         lib.oracle_order.restype = ctypes.c_int32
         lib.oracle_bruteforce.argtypes = [vp] + q + [i32p, ctypes.c_int64]
         lib.oracle_bruteforce.restype = ctypes.c_int64
+        lib.oracle_enumerate_hom.argtypes = [vp] + q + [i32p, ctypes.c_int64, ctypes.c_int32, u64p]
+        lib.oracle_enumerate_hom.restype = ctypes.c_int64
+        lib.oracle_bruteforce_hom.argtypes = [vp] + q + [i32p, ctypes.c_int64]
+        lib.oracle_bruteforce_hom.restype = ctypes.c_int64
         lib.oracle_murmur3_32.argtypes = [u8p, ctypes.c_int32, ctypes.c_uint32]
         lib.oracle_murmur3_32.restype = ctypes.c_uint32
         lib.oracle_data_signatures.argtypes = [vp, u32p]
@@ -115,30 +119,36 @@ def _qargs(q):
     return (vl, s, d, e), [int(vl.shape[0]), _i32(vl), _i32(s), _i32(d), _i32(e), int(s.shape[0])]
 
 
-def enumerate_rows(g: OracleGraph, q, max_rows: int | None = None) -> np.ndarray:
-    """All embeddings (rows in query-vertex order), sorted lexicographically."""
+def _enum_fn(hom: bool):
+    lib = _load()
+    return lib.oracle_enumerate_hom if hom else lib.oracle_enumerate
+
+
+def enumerate_rows(g: OracleGraph, q, max_rows: int | None = None, hom: bool = False) -> np.ndarray:
+    """All embeddings (homomorphisms with hom=True; rows in query-vertex
+    order), sorted lexicographically."""
     keep, a = _qargs(q)
     k = a[0]
-    lib = _load()
+    fn = _enum_fn(hom)
     if max_rows is None:
-        cnt = lib.oracle_enumerate(g._h, *a, None, 0, 1, None)
+        cnt = fn(g._h, *a, None, 0, 1, None)
         if cnt < 0:
             raise ValueError("invalid query")
         max_rows = cnt
     out = np.empty((max(max_rows, 1), k), np.int32)
-    cnt = lib.oracle_enumerate(g._h, *a, _i32(out), max_rows, 1, None)
+    cnt = fn(g._h, *a, _i32(out), max_rows, 1, None)
     if cnt < 0:
         raise ValueError("invalid query")
     rows = out[:min(cnt, max_rows)]
     return sort_rows(rows)
 
 
-def count(g: OracleGraph, q, nthreads: int | None = None) -> tuple[int, tuple[int, int, int]]:
+def count(g: OracleGraph, q, nthreads: int | None = None, hom: bool = False) -> tuple[int, tuple[int, int, int]]:
     """(count, fingerprint) with nthreads workers over the first position's candidates."""
     keep, a = _qargs(q)
     fp = (ctypes.c_uint64 * 3)()
     nt = _threads() if nthreads is None else nthreads
-    cnt = _load().oracle_enumerate(g._h, *a, None, 0, nt, fp)
+    cnt = _enum_fn(hom)(g._h, *a, None, 0, nt, fp)
     if cnt < 0:
         raise ValueError("invalid query")
     return int(cnt), (int(fp[0]), int(fp[1]), int(fp[2]))
@@ -152,15 +162,16 @@ def order(q) -> np.ndarray:
     return out
 
 
-def bruteforce_rows(g: OracleGraph, q) -> np.ndarray:
+def bruteforce_rows(g: OracleGraph, q, hom: bool = False) -> np.ndarray:
     keep, a = _qargs(q)
     k = a[0]
     lib = _load()
-    cnt = lib.oracle_bruteforce(g._h, *a, None, 0)
+    fn = lib.oracle_bruteforce_hom if hom else lib.oracle_bruteforce
+    cnt = fn(g._h, *a, None, 0)
     if cnt < 0:
         raise ValueError("invalid query")
     out = np.empty((max(cnt, 1), k), np.int32)
-    lib.oracle_bruteforce(g._h, *a, _i32(out), cnt)
+    fn(g._h, *a, _i32(out), cnt)
     return sort_rows(out[:cnt])
 
 

@@ -14,6 +14,10 @@
  *                      Recursive backtracking in BFS order of Q from vertex 0.
  *   oracle_bruteforce  The same definition by exhaustive enumeration of every
  *                      injective map (tiny inputs only); used to pin the above.
+ *   oracle_enumerate_hom, oracle_bruteforce_hom
+ *                      Sec. VII-A: homomorphism semantics drops injectivity
+ *                      (two query vertices may map to one data vertex); the
+ *                      same backtracking and exhaustive check without it.
  *   oracle_signature   Sec. III-A: N = 512-bit vertex signature.  The first
  *                      K = 32 bits hold the vertex label itself (Sec. VII-B
  *                      says single labels are stored directly); the other 480
@@ -149,6 +153,7 @@ typedef struct {
     int32_t nback[32];            /* earlier-positioned neighbours of order[p] */
     int32_t back_pos[32][32];
     int32_t back_lab[32][32];
+    int injective;                /* 1: isomorphism (Defs. 2-3); 0: homomorphism (Sec. VII-A) */
 } plan_t;
 
 typedef struct {
@@ -173,7 +178,8 @@ static int feasible(const enum_state_t *s, int p, int32_t w) {
     const plan_t *pl = s->pl;
     const og_t *g = pl->g;
     if (g->vlab[w] != pl->q->vlab[pl->order[p]]) return 0;
-    for (int i = 0; i < p; ++i) if (s->f[i] == w) return 0;                 /* injective */
+    if (pl->injective)
+        for (int i = 0; i < p; ++i) if (s->f[i] == w) return 0;             /* injective */
     for (int b = 0; b < pl->nback[p]; ++b)                                   /* every query edge */
         if (edge_label(g, s->f[pl->back_pos[p][b]], w) != pl->back_lab[p][b]) return 0;
     return 1;
@@ -197,6 +203,7 @@ static void extend(enum_state_t *s, int p) {
 
 static void make_plan(plan_t *pl, const og_t *g, const oq_t *q) {
     pl->g = g; pl->q = q;
+    pl->injective = 1;
     int32_t seen[32] = {0};
     int32_t tail = 0;
     for (int32_t root = 0; root < q->k; ++root) {
@@ -240,14 +247,15 @@ static void *enum_worker(void *arg) {
  * first max_rows embeddings when out != NULL; rows are only written when
  * nthreads == 1.  fp[0..2] receives (count, sum h, xor h).
  */
-int64_t oracle_enumerate(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
-                         const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows, int32_t nthreads,
-                         uint64_t *fp) {
+static int64_t enumerate_maps(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                              const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows, int32_t nthreads,
+                              uint64_t *fp, int injective) {
     const og_t *g = (const og_t *)gp;
     oq_t q;
     if (make_query(&q, k, qvlab, qsrc, qdst, qelab, qm)) return -1;
     plan_t pl;
     make_plan(&pl, g, &q);
+    pl.injective = injective;
     int64_t count = 0; uint64_t s = 0, x = 0;
     if (nthreads <= 1) {
         enum_state_t st;
@@ -274,6 +282,20 @@ int64_t oracle_enumerate(void *gp, int32_t k, const int32_t *qvlab, const int32_
     return count;
 }
 
+int64_t oracle_enumerate(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                         const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows, int32_t nthreads,
+                         uint64_t *fp) {
+    return enumerate_maps(gp, k, qvlab, qsrc, qdst, qelab, qm, out, max_rows, nthreads, fp, 1);
+}
+
+/* All homomorphisms of Q in G (Sec. VII-A): as oracle_enumerate without
+ * injectivity. */
+int64_t oracle_enumerate_hom(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                             const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows, int32_t nthreads,
+                             uint64_t *fp) {
+    return enumerate_maps(gp, k, qvlab, qsrc, qdst, qelab, qm, out, max_rows, nthreads, fp, 0);
+}
+
 /* Matching order used by oracle_enumerate (for tests). */
 int32_t oracle_order(int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
                      const int32_t *qelab, int32_t qm, int32_t *order_out) {
@@ -289,19 +311,19 @@ int32_t oracle_order(int32_t k, const int32_t *qvlab, const int32_t *qsrc, const
  * Exhaustive check of every injective map f: V(Q) -> V(G) (n!/(n-k)! maps),
  * in lexicographic order of (f(0), ..., f(k-1)).  Tiny inputs only.
  */
-int64_t oracle_bruteforce(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
-                          const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows) {
+static int64_t bruteforce_maps(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                               const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows, int injective) {
     const og_t *g = (const og_t *)gp;
     oq_t q;
     if (make_query(&q, k, qvlab, qsrc, qdst, qelab, qm)) return -1;
     int32_t f[32];
     int64_t count = 0;
     int32_t n = g->n;
-    if (k > n) return 0;
+    if (injective && k > n) return 0;
     for (int i = 0; i < k; ++i) f[i] = 0;
     for (;;) {
         int ok = 1;
-        for (int i = 0; i < k && ok; ++i)
+        for (int i = 0; i < k && ok && injective; ++i)
             for (int j = i + 1; j < k; ++j) if (f[i] == f[j]) { ok = 0; break; }
         for (int i = 0; i < k && ok; ++i) if (g->vlab[f[i]] != q.vlab[i]) ok = 0;
         for (int i = 0; i < k && ok; ++i)
@@ -317,6 +339,18 @@ int64_t oracle_bruteforce(void *gp, int32_t k, const int32_t *qvlab, const int32
         f[i]++;
     }
     return count;
+}
+
+int64_t oracle_bruteforce(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                          const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows) {
+    return bruteforce_maps(gp, k, qvlab, qsrc, qdst, qelab, qm, out, max_rows, 1);
+}
+
+/* Every map f: V(Q) -> V(G) (n^k maps) checked against the homomorphism
+ * definition (Sec. VII-A).  Tiny inputs only. */
+int64_t oracle_bruteforce_hom(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                              const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows) {
+    return bruteforce_maps(gp, k, qvlab, qsrc, qdst, qelab, qm, out, max_rows, 0);
 }
 
 /* ------------------------------------------------------------- signature */

@@ -294,3 +294,50 @@ def test_fingerprint_is_order_independent():
     assert fp == oracle.fingerprint(rows[rng.permutation(500)])
     assert fp != oracle.fingerprint(rows[:-1])
     assert fp[0] == 500
+
+
+# ------------------------------------------------- homomorphism (Sec. VII-A)
+@pytest.mark.parametrize("block", range(4))
+def test_homomorphism_backtracking_equals_bruteforce(block):
+    """Sec. VII-A: without injectivity, backtracking equals the exhaustive
+    check of all n^k maps (400 cases)."""
+    rng = np.random.default_rng(2000 + block)
+    for case in range(100):
+        n = int(rng.integers(3, 8))
+        g = H.random_graph(rng, n, float(rng.uniform(0.2, 0.8)), int(rng.integers(1, 3)), int(rng.integers(1, 3)))
+        k = int(rng.integers(1, 5))
+        q = H.random_connected_query(rng, k, int(rng.integers(0, 3)), int(rng.integers(1, 3)),
+                                     int(rng.integers(1, 3)))
+        G = og(g)
+        got = oracle.enumerate_rows(G, q, hom=True)
+        want = oracle.bruteforce_rows(G, q, hom=True)
+        assert np.array_equal(got, want), (block, case)
+        c, fp = oracle.count(G, q, nthreads=3, hom=True)
+        assert c == want.shape[0] and fp == oracle.fingerprint(want)
+        # every embedding is a homomorphism; a clique query has no others
+        iso = oracle.enumerate_rows(G, q)
+        assert iso.shape[0] <= want.shape[0]
+        if len(q.src) == k * (k - 1) // 2:
+            assert np.array_equal(iso, want)
+
+
+def test_homomorphism_closed_forms():
+    """Unlabelled: hom(edge) = 2|E|, hom(path of k vertices) = 1^T A^(k-1) 1
+    (walks), hom(star K_1,s) = sum_v deg(v)^s, hom(C4) = trace(A^4)."""
+    rng = np.random.default_rng(11)
+    for _ in range(6):
+        g = H.random_graph(rng, 18, float(rng.uniform(0.1, 0.5)), 1, 1)
+        G = og(g)
+        A = np.zeros((g.n, g.n), np.int64)
+        A[g.src, g.dst] = 1
+        A[g.dst, g.src] = 1
+        one = np.ones(g.n, np.int64)
+        deg = A.sum(axis=1)
+        assert oracle.count(G, H.path_query(2), hom=True)[0] == 2 * g.m
+        for k in (3, 4, 5):
+            want = int(one @ np.linalg.matrix_power(A, k - 1) @ one)
+            assert oracle.count(G, H.path_query(k), hom=True)[0] == want
+        for s in (2, 3):
+            assert oracle.count(G, H.star_query(s), hom=True)[0] == int((deg ** s).sum())
+        c4 = H.query(4, [(0, 1), (1, 2), (2, 3), (0, 3)])
+        assert oracle.count(G, c4, hom=True)[0] == int(np.trace(np.linalg.matrix_power(A, 4)))
