@@ -128,7 +128,12 @@ typedef struct {
     int32_t k;
 } gsi_stats;
 
-typedef enum { GSI_ISOMORPHISM = 0 } gsi_semantics;
+/* Query semantics.  GSI_ISOMORPHISM: Defs. 2-3 (injective maps).
+ * GSI_HOMOMORPHISM: Sec. VII-A, the set subtraction of Alg. 3 dropped (two
+ * query vertices may map to one data vertex); the filter then uses only the
+ * "at least one" signature states, the "at least two" state being unsound
+ * without injectivity.  Batches and servers run isomorphism only. */
+typedef enum { GSI_ISOMORPHISM = 0, GSI_HOMOMORPHISM = 1 } gsi_semantics;
 
 typedef struct {
     void *stream;            /* stream for all device work of the query */
@@ -137,7 +142,7 @@ typedef struct {
     uint64_t mem_budget;     /* bytes for intermediate tables; 0 = 40% of the
                                 device's memory */
     int32_t count_only;      /* 1: count embeddings, materialise none */
-    int32_t semantics;       /* GSI_ISOMORPHISM */
+    int32_t semantics;       /* gsi_semantics (0 = isomorphism) */
     const int32_t *order;    /* optional join order (k query vertex ids, each
                                 connected to an earlier one); NULL = Alg. 2 */
     gsi_stats *stats;        /* optional: timing and work counters */

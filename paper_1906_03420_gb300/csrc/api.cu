@@ -160,7 +160,7 @@ gsi_status gsi_query_run(gsi_graph *g, const int32_t *qvlab, int32_t k, const in
     gsi_query_opts o;
     std::memset(&o, 0, sizeof o);
     if (opts) o = *opts;
-    if (o.semantics != GSI_ISOMORPHISM) {
+    if (o.semantics != GSI_ISOMORPHISM && o.semantics != GSI_HOMOMORPHISM) {
         set_error("gsi_query_run: unsupported semantics");
         return GSI_EINVAL;
     }

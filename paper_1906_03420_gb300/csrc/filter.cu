@@ -111,7 +111,7 @@ struct SeedWriter {
 }  // namespace
 
 void query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
-                      const int32_t *qelab, int32_t qm, QuerySig *out) {
+                      const int32_t *qelab, int32_t qm, QuerySig *out, bool hom) {
     out->k = k;
     uint32_t counts[GSI_MAX_QUERY_VERTICES][GSI_SIG_GROUPS];
     for (int u = 0; u < k; ++u)
@@ -126,7 +126,7 @@ void query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, cons
         out->sig[u][0] = (uint32_t)qvlab[u];
         for (uint32_t gidx = 0; gidx < GSI_SIG_GROUPS; ++gidx) {
             if (counts[u][gidx] >= 1) out->sig[u][sig_word(gidx)] |= 1u << sig_bit(gidx);
-            if (counts[u][gidx] >= 2) out->sig[u][sig_word(gidx)] |= 2u << sig_bit(gidx);
+            if (counts[u][gidx] >= 2 && !hom) out->sig[u][sig_word(gidx)] |= 2u << sig_bit(gidx);
         }
     }
 }

@@ -52,8 +52,9 @@ struct QuerySig {
     int32_t k = 0;
     uint32_t sig[GSI_MAX_QUERY_VERTICES][GSI_SIG_WORDS];
 };
+// hom: homomorphism semantics keeps only the "at least one" group states.
 void query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,
-                      const int32_t *qelab, int32_t qm, QuerySig *out);
+                      const int32_t *qelab, int32_t qm, QuerySig *out, bool hom = false);
 // bitmaps: device uint32[k][nwords]; counts: device unsigned long long[k] (both zeroed here).
 gsi_status launch_filter(const gsi_graph *g, const QuerySig &q, uint32_t *bitmaps, unsigned long long *counts,
                          cudaStream_t st);
@@ -91,6 +92,7 @@ struct JoinStep {
     int32_t col[GSI_MAX_QUERY_VERTICES];
     int32_t lab[GSI_MAX_QUERY_VERTICES];
     int32_t perm[GSI_MAX_QUERY_VERTICES + 1];   // output position of each column
+    int32_t hom = 0;                     // 1: homomorphism (no set subtraction, Sec. VII-A)
 };
 
 constexpr int JOIN_NT = 256;

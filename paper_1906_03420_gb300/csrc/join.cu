@@ -314,6 +314,7 @@ StepDev step_dev(const gsi_graph *g, const JoinStep &s) {
     d.d = s.d;
     d.L = g->L;
     d.ulab = s.ulab;
+    d.hom = s.hom;
     for (int i = 0; i < GSI_MAX_QUERY_VERTICES; ++i) {
         d.col[i] = i < s.d ? s.col[i] : 0;
         d.lab[i] = i < s.d ? s.lab[i] : 0;

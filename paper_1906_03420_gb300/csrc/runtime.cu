@@ -569,7 +569,8 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     }
 
     QuerySig qs;
-    query_signatures(q.vl.data(), q.k, q.src.data(), q.dst.data(), q.lab.data(), q.qm, &qs);
+    const bool hom = o.semantics == GSI_HOMOMORPHISM;
+    query_signatures(q.vl.data(), q.k, q.src.data(), q.dst.data(), q.lab.data(), q.qm, &qs, hom);
     const uint64_t bm_words = (uint64_t)q.k * (uint64_t)g->nwords;
     // per-thread pinned staging for small readbacks (cudaFreeHost would
     // synchronise the whole device, so the buffer lives as long as the thread)
@@ -636,6 +637,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     if (rc == GSI_OK && !empty) {
         for (int p = 0; p < q.k; ++p) x.order[p] = order[p];
         make_steps(q, order, first, ranks, x.steps);
+        for (JoinStep &js : x.steps) js.hom = hom ? 1 : 0;
         // device-driven path first; the host-driven splitting path on overflow
         bool overflow = true;
         if (!o.host_driven && q.k > 1) {

@@ -17,6 +17,7 @@ import numpy as np
 from . import _build
 
 GSI_OK, GSI_EINVAL, GSI_ENOMEM, GSI_ECAPPED, GSI_ETIMEOUT, GSI_ECANCELLED, GSI_ECUDA, GSI_EBUSY = range(8)
+GSI_ISOMORPHISM, GSI_HOMOMORPHISM = 0, 1
 STATUS_NAMES = {0: "GSI_OK", 1: "GSI_EINVAL", 2: "GSI_ENOMEM", 3: "GSI_ECAPPED", 4: "GSI_ETIMEOUT",
                 5: "GSI_ECANCELLED", 6: "GSI_ECUDA", 7: "GSI_EBUSY"}
 MAX_QUERY_VERTICES = 32
@@ -321,14 +322,14 @@ class Graph:
         return out
 
     def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
-              order=None, stats: c_stats | None = None, host_driven: bool = False) -> Result:
+              order=None, stats: c_stats | None = None, host_driven: bool = False, semantics: int = 0) -> Result:
         qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
         o = c_query_opts()
         o.stream = _stream_handle(stream)
         o.row_cap = row_cap
         o.mem_budget = mem_budget
         o.count_only = int(count_only)
-        o.semantics = 0
+        o.semantics = int(semantics)
         o.host_driven = int(host_driven)
         ordr = None
         if order is not None:
