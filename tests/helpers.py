@@ -150,3 +150,27 @@ def falling(x, k):
     for i in range(k):
         r *= (x - i)
     return r if x >= k else 0
+
+
+def worked_example():
+    """(printed facts, graph, query) of the Sec. IV worked example fixture."""
+    import os
+    facts, vl, E, qvl, QE = {}, None, [], None, []
+    path = os.path.join(os.path.dirname(__file__), "golden", "worked_example.txt")
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "fact":
+            facts[f[1]] = [int(x) for x in f[2:]]
+        elif f[0] == "vlab":
+            vl = [int(x) for x in f[1:]]
+        elif f[0] == "e":
+            E.append(tuple(int(x) for x in f[1:]))
+        elif f[0] == "qvlab":
+            qvl = [int(x) for x in f[1:]]
+        elif f[0] == "qe":
+            QE.append(tuple(int(x) for x in f[1:]))
+    g = graph(len(vl), [(a, b) for a, b, _ in E], vl, [l for _, _, l in E])
+    q = query(len(qvl), [(a, b) for a, b, _ in QE], qvl, [l for _, _, l in QE])
+    return facts, g, q

@@ -412,3 +412,15 @@ def test_relabelling_invariance(pkg):
         a = oracle.sort_rows(G1.query(q).rows())
         b = oracle.sort_rows(np.argsort(perm).astype(np.int32)[G2.query(q).rows()])
         assert np.array_equal(a, b)
+
+
+def test_worked_example_on_gpu(pkg):
+    """The Sec. IV worked example (tests/golden): one join step from
+    M = {(v0, v_i)} leaves (v0, v100, v201); the full query finds the single
+    printed match."""
+    facts, g, q = H.worked_example()
+    G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
+    assert G.query(q).rows().tolist() == [facts["match"]]
+    M = np.array([(0, i) for i in range(1, 101)], np.int32)
+    cnt, rows = _gpu_step(pkg, G, M, g.vlab == 2, 2, [1, 0], [0, 1])   # linking edges u1u2:a, u0u2:b
+    assert cnt == 1 and rows.tolist() == [[0, 100] + facts["buf99_final"]]

@@ -341,3 +341,32 @@ def test_homomorphism_closed_forms():
             assert oracle.count(G, H.star_query(s), hom=True)[0] == int((deg ** s).sum())
         c4 = H.query(4, [(0, 1), (1, 2), (2, 3), (0, 3)])
         assert oracle.count(G, c4, hom=True)[0] == int(np.trace(np.linalg.matrix_power(A, 4)))
+
+
+# ------------------------------------------------------- worked example (Sec. IV)
+def test_worked_example_fixture_holds_the_printed_facts():
+    """The constructed graph satisfies every Prealloc fact Sec. IV-C prints."""
+    facts, g, q = H.worked_example()
+    G = og(g)
+    nbr = lambda v, l: sorted(w for w in range(g.n) if w != v and G.edge_label(v, w) == l)
+    rows = [(0, i) for i in range(1, 101)]                     # matches of u0u1 (label a)
+    caps_a = [len(nbr(v1, 0)) for _, v1 in rows]               # first edge u1u2, label a
+    caps_b = [len(nbr(v0, 1)) for v0, _ in rows]               # first edge u0u2, label b
+    assert sum(caps_a) == facts["gba_u1u2"][0]
+    assert sum(caps_a[:99]) == facts["buf99_offset"][0] and caps_a[99] == facts["num_L99_a"][0]
+    assert sum(caps_b) == facts["gba_u0u2"][0]
+    assert [w for w in nbr(100, 0) if w not in (0, 100)] == facts["buf99_subtracted"]
+
+
+def test_worked_example_oracle_join_and_match():
+    """Alg. 3 on the example: joining u2 to M = {(v0, v_i)} leaves only
+    buf99 = {v201}; the full search returns the single printed match."""
+    facts, g, q = H.worked_example()
+    G = og(g)
+    M = np.array([(0, i) for i in range(1, 101)], np.int32)
+    in_c = np.array(g.vlab == 2, np.uint8)                     # C(u2) = the label-C vertices
+    got = oracle.join_step(G, M, in_c, [1, 0], [0, 1])         # linking edges u1u2:a, u0u2:b
+    assert got.tolist() == [[0, 100] + facts["buf99_final"]]
+    assert oracle.enumerate_rows(G, q).tolist() == [facts["match"]]
+    member, _ = oracle.filter_sets(G, q)                       # the match survives the filter
+    assert all(member[u, v] for u, v in enumerate(facts["match"]))
