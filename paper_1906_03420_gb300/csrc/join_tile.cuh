@@ -51,23 +51,6 @@ __device__ inline uint32_t row_bound(const StepDev &s, const int32_t *row, const
     return best;
 }
 
-// row_bound plus the summed length of the row's label sub-lists (for the
-// algorithmic-byte count).
-__device__ inline uint32_t row_bound_sum(const StepDev &s, const int32_t *row, const uint32_t *__restrict__ off,
-                                         const uint16_t *__restrict__ cl, uint64_t *lsum) {
-    uint32_t best = 0xffffffffu;
-    uint64_t sum = 0;
-    for (int j = 0; j < s.d; ++j) {
-        uint64_t seg = (uint64_t)(uint32_t)__ldcg(row + s.col[j]) * (uint64_t)s.L + (uint64_t)s.lab[j];
-        uint32_t a = __ldg(off + seg), b = __ldg(off + seg + 1), lo, hi;
-        label_range(cl, a, b, (uint32_t)s.ulab, &lo, &hi);
-        best = min(best, hi - lo);
-        sum += hi - lo;
-    }
-    *lsum = sum;
-    return best;
-}
-
 // Bits of a per-row bound record: the shortest sub-list's length in the low
 // 27 bits, the index of its linking edge above (lists stay below 2^27).
 constexpr uint32_t BOUND_LEN_BITS = 27;
