@@ -11,6 +11,7 @@
 // bitmap word (consecutive, as ids ascend) OR their bits together and the
 // last of them sets them with one atomicOr.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -163,8 +164,19 @@ gsi_status filter_plan(const gsi_graph *g, const std::vector<const uint32_t *> &
         }
         i = j;
     }
-    // up to 96 KB of per-CTA counters (set here, outside any stream capture)
-    GSI_CUDA_TRY(cudaFuncSetAttribute(k_filter_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    // up to 96 KB of per-CTA counters (set once per device, outside any
+    // stream capture)
+    {
+        static std::once_flag once[64];
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaError_t e = cudaSuccess;
+        if (dev >= 0 && dev < 64)
+            std::call_once(once[dev], [&e]() {
+                e = cudaFuncSetAttribute(k_filter_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+            });
+        GSI_CUDA_TRY(e);
+    }
     fp->ngroups = (int32_t)wbeg.size();
     fp->nq = (int32_t)qid.size();
     fp->warps = warps;

@@ -144,17 +144,18 @@ size_t join_args_size();
 // expects one CTA more than it has, so every wait must run out.  Returns
 // GSI_ETIMEOUT when the kernel reported that, GSI_OK otherwise.
 gsi_status selftest_barrier_timeout(int dev, unsigned long long spin_limit, double *ms);
-// Seed + every join step of one query in one cooperative launch.  cfg_dev:
-// join_args_size() * k bytes; dsteps: k records (host-initialised static
-// fields); bsum: QUERY_MAX_CTAS words.  steps[0].count receives |seed|.
-gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
-                             const int32_t *order, int count_only, unsigned long long *stats, void *cfg_dev,
+// Seed + every join step of one query in one cooperative launch, in two
+// parts.  query_coop_configs writes the k step configurations
+// (join_args_size() * k bytes) to cfg_host and returns the dynamic shared
+// memory the launch needs; the caller uploads them to cfg_dev together with
+// the k step records (host-initialised static fields) and the zeroed control
+// words.  launch_query_coop then launches; bsum: QUERY_MAX_CTAS words.
+// steps[0].count receives |seed|.
+gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
+                              const int32_t *order, int count_only, unsigned long long *stats, void *cfg_host,
+                              size_t *smem);
+gsi_status launch_query_coop(const gsi_graph *g, int k, const uint32_t *seed_bitmap, size_t smem, void *cfg_dev,
                              DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out,
                              cudaStream_t stream);
-// fail bits: 1 = scratch region too small, 2 = a table overflowed its region.
-gsi_status launch_step_device(const gsi_graph *g, const JoinStep &s, DStep *st, unsigned *fail, const uint32_t *cand,
-                              int count_only, unsigned long long *stats, cudaStream_t stream);
-gsi_status launch_join_device(const gsi_graph *g, const JoinStep &s, DStep *st, unsigned *fail, const uint32_t *cand,
-                              int count_only, unsigned long long *stats, cudaStream_t stream);
 
 }  // namespace gsi

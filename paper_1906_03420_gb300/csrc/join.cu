@@ -37,6 +37,8 @@
 //     join runs once; the output buffer is sized by F's total).
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -405,11 +407,11 @@ JoinArgs make_join_args(const gsi_graph *g, const JoinStep &s, const uint32_t *c
 
 size_t join_args_size() { return sizeof(JoinArgs); }
 
-gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
-                             const int32_t *order, int count_only, unsigned long long *stats, void *cfg_dev,
-                             DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out, cudaStream_t st) {
-    // per-step configuration, uploaded next to the step records
-    std::vector<JoinArgs> cfg((size_t)k);
+gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
+                              const int32_t *order, int count_only, unsigned long long *stats, void *cfg_host,
+                              size_t *smem) {
+    JoinArgs *cfg = static_cast<JoinArgs *>(cfg_host);
+    std::memset(cfg, 0, sizeof(JoinArgs));
     size_t sm = 0;
     for (int t = 1; t < k; ++t) {
         const int co = (t == k - 1) && count_only;
@@ -420,19 +422,37 @@ gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &st
         set_error("join: shared memory need exceeds 200 KB");
         return GSI_EINVAL;
     }
-    GSI_CUDA_TRY(cudaMemcpyAsync(cfg_dev, cfg.data(), sizeof(JoinArgs) * (size_t)k, cudaMemcpyHostToDevice, st));
+    *smem = sm;
+    return GSI_OK;
+}
+
+gsi_status launch_query_coop(const gsi_graph *g, int k, const uint32_t *seed_bitmap, size_t sm, void *cfg_dev,
+                             DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out,
+                             cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
-    static int attr_set[64];
+    // occupancy depends only on the dynamic shared memory: looked up once per
+    // (device, size), as are the function attribute and the SM count
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, int> occ;
     static int nsm[64];
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        GSI_CUDA_TRY(cudaFuncSetAttribute(k_query<JOIN_NT, JOIN_VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024));
-        GSI_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
-        attr_set[dev] = 1;
-    }
     int per_sm = 0;
-    GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<JOIN_NT, JOIN_VT>, JOIN_NT, sm));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !nsm[dev]) {
+            GSI_CUDA_TRY(cudaFuncSetAttribute(k_query<JOIN_NT, JOIN_VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              200 * 1024));
+            GSI_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
+        }
+        auto it = occ.find({dev, sm});
+        if (it != occ.end()) {
+            per_sm = it->second;
+        } else {
+            GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<JOIN_NT, JOIN_VT>, JOIN_NT,
+                                                                       sm));
+            occ[{dev, sm}] = per_sm;
+        }
+    }
     if (per_sm < 1) {
         set_error("join: the query kernel does not fit on an SM");
         return GSI_EINVAL;
@@ -442,9 +462,8 @@ gsi_status launch_query_coop(const gsi_graph *g, const std::vector<JoinStep> &st
     if (grid > QUERY_MAX_CTAS) grid = QUERY_MAX_CTAS;
     *grid_out = grid;
     const JoinArgs *cfgp = static_cast<const JoinArgs *>(cfg_dev);
-    const uint32_t *seed_bm = bitmaps + (uint64_t)order[0] * (uint64_t)g->nwords;
     int64_t nwords = g->nwords;
-    void *args[] = {(void *)&cfgp, (void *)&dsteps, (void *)&k, (void *)&ctl, (void *)&seed_bm, (void *)&nwords,
+    void *args[] = {(void *)&cfgp, (void *)&dsteps, (void *)&k, (void *)&ctl, (void *)&seed_bitmap, (void *)&nwords,
                     (void *)&bsum};
     GSI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_query<JOIN_NT, JOIN_VT>, dim3(grid), dim3(JOIN_NT), args,
                                              sm, st));

@@ -1,6 +1,7 @@
 // Host runtime behind the C ABI: graph objects, query validation, the Alg. 2
 // planner, the memory-bounded depth-first join driver and result objects.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -420,8 +421,24 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     QueryCtl *qc = reinterpret_cast<QueryCtl *>(p);
     p += 256;
     unsigned long long *bsum = reinterpret_cast<unsigned long long *>(p);
-    std::vector<DStep> hs((size_t)k);
-    std::memset(hs.data(), 0, sizeof(DStep) * (size_t)k);
+    // configurations, step records and zeroed control words staged in pinned
+    // memory in the control block's layout: one upload, no staging copies
+    const size_t up_bytes = (size_t)(p - ctl);
+    if (up_bytes > h_stage_bytes) {
+        release();
+        set_error("device-driven join: control block larger than the staging buffer");
+        return GSI_EINVAL;
+    }
+    unsigned long long *jstats = stats ? d_scalars + 1 : nullptr;
+    size_t smem = 0;
+    rc = query_coop_configs(g, steps, k, bitmaps, order, count_only, jstats, h_stage, &smem);
+    if (rc != GSI_OK) {
+        release();
+        return rc;
+    }
+    DStep *hs = reinterpret_cast<DStep *>(h_stage + (reinterpret_cast<unsigned char *>(dst) - ctl));
+    std::memset(hs, 0, sizeof(DStep) * (size_t)k);
+    std::memset(h_stage + (reinterpret_cast<unsigned char *>(qc) - ctl), 0, 256);
     for (int t = 1; t < k; ++t) {
         DStep &h = hs[t];
         h.M = reg[(t - 1) & 1];
@@ -435,16 +452,15 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
         h.t = t;
     }
     rc = GSI_OK;
-    if (cudaMemcpyAsync(dst, hs.data(), sizeof(DStep) * (size_t)k, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(qc, 0, sizeof(QueryCtl), st) != cudaSuccess) {
+    if (cudaMemcpyAsync(ctl, h_stage, up_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         set_error("device-driven join: control upload failed");
         rc = GSI_ECUDA;
     }
-    unsigned long long *jstats = stats ? d_scalars + 1 : nullptr;
     int grid = 0;
     if (rc == GSI_OK) {
         tm.begin(1);
-        rc = launch_query_coop(g, steps, k, bitmaps, order, count_only, jstats, cfg_dev, dst, qc, bsum, &grid, st);
+        rc = launch_query_coop(g, k, bitmaps + (uint64_t)order[0] * (uint64_t)g->nwords, smem, cfg_dev, dst, qc, bsum,
+                               &grid, st);
         tm.end();
         kernels += 1;
         tiles += (uint64_t)(k - 1);
@@ -543,9 +559,16 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         x.budget = o.mem_budget;
     } else {
         // a fixed share of the device (not of the momentarily free memory, which
-        // excludes blocks the stream-ordered pool keeps cached for reuse)
-        size_t fr = 0, totm = 0;
-        GSI_CUDA_TRY(cudaMemGetInfo(&fr, &totm));
+        // excludes blocks the stream-ordered pool keeps cached for reuse); the
+        // device's total is looked up once
+        static std::atomic<uint64_t> total_mem[64];
+        uint64_t totm = g->device >= 0 && g->device < 64 ? total_mem[g->device].load() : 0;
+        if (!totm) {
+            size_t fr = 0, t2 = 0;
+            GSI_CUDA_TRY(cudaMemGetInfo(&fr, &t2));
+            totm = t2;
+            if (g->device >= 0 && g->device < 64) total_mem[g->device].store(totm);
+        }
         x.budget = (uint64_t)(0.4 * (double)totm);
     }
     // a query edge label that no data edge carries: no embeddings
@@ -572,11 +595,16 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     const bool hom = o.semantics == GSI_HOMOMORPHISM;
     query_signatures(q.vl.data(), q.k, q.src.data(), q.dst.data(), q.lab.data(), q.qm, &qs, hom);
     const uint64_t bm_words = (uint64_t)q.k * (uint64_t)g->nwords;
-    // per-thread pinned staging for small readbacks (cudaFreeHost would
-    // synchronise the whole device, so the buffer lives as long as the thread)
-    static thread_local uint64_t *t_pinned = nullptr;
-    if (!t_pinned) GSI_CUDA_TRY(cudaMallocHost(&t_pinned, 8 * (GSI_MAX_QUERY_VERTICES + 8)));
-    x.h_pinned = t_pinned;
+    // per-thread pinned staging: small readbacks first, then the upload area
+    // of the device-driven control block (cudaFreeHost would synchronise the
+    // whole device, so the buffer lives as long as the thread).  Every use is
+    // complete before run_query returns (the stream is synchronised).
+    static thread_local unsigned char *t_pinned = nullptr;
+    constexpr size_t PINNED_READ = 4096, PINNED_STAGE = 60 * 1024;
+    if (!t_pinned) GSI_CUDA_TRY(cudaMallocHost(&t_pinned, PINNED_READ + PINNED_STAGE));
+    x.h_pinned = reinterpret_cast<uint64_t *>(t_pinned);
+    x.h_stage = t_pinned + PINNED_READ;
+    x.h_stage_bytes = PINNED_STAGE;
     unsigned long long *d_counts = nullptr;
     GSI_TRY(dalloc(x, (void **)&x.bitmaps, bm_words * 4));
     GSI_TRY(dalloc(x, (void **)&d_counts, 8 * GSI_MAX_QUERY_VERTICES + 32));

@@ -72,7 +72,9 @@ struct Exec {
     std::vector<JoinStep> steps;     // steps[t] extends a t-column table
     uint32_t *bitmaps = nullptr;     // [k][nwords], indexed by query vertex id
     unsigned long long *d_scalars = nullptr;   // [0] step count, [1] bytes, [2] items
-    uint64_t *h_pinned = nullptr;
+    uint64_t *h_pinned = nullptr;             // pinned readback words
+    unsigned char *h_stage = nullptr;         // pinned upload staging
+    size_t h_stage_bytes = 0;
     uint64_t budget = 0, live = 0, peak = 0, tiles = 0;
     uint64_t row_cap = 0;
     int count_only = 0;
