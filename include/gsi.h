@@ -89,8 +89,10 @@ typedef struct {
  * Load G into device memory and build its label-partitioned CSR (the
  * edge-label-partitioned graphs P(G,l) of Sec. IV in the "basic
  * representation": one row-offset entry per (vertex, label)), the per-label
- * edge frequencies freq(l) (Table "Notations") and the column-first signature
- * table (Sec. III-A).
+ * edge frequencies freq(l) (Table "Notations"), the column-first signature
+ * table (Sec. III-A) and a copy of it grouped by vertex label (vertex ids of
+ * each label in ascending order, groups padded to multiples of 32), which the
+ * filter reads.
  *   vlab  int32[n]   vertex labels (any int32)
  *   src, dst, elab  int32[m]   edge i = {src[i], dst[i]} with label elab[i] >= 0
  * Errors: GSI_EINVAL for n < 1, m < 0, an id outside [0,n), a self-loop, a
@@ -117,8 +119,12 @@ typedef struct {
     uint64_t filter_launches, join_launches, other_launches;
     uint64_t filter_bytes;   /* algorithmic bytes of the filter */
     uint64_t join_bytes;     /* algorithmic bytes of the join steps */
-    uint64_t join_items;     /* candidates examined: sum of |N(v'_i, l0)| */
-    uint64_t tiles;          /* row ranges processed (memory-bounded splits) */
+    uint64_t join_items;     /* candidate slots: sum over rows of the length
+                                of the row's shortest linking list restricted
+                                to the new vertex's label (a bound at most
+                                Alg. 4's) */
+    uint64_t tiles;          /* row ranges processed (memory-bounded splits);
+                                for batches, work units processed */
     uint64_t peak_bytes;     /* peak intermediate-table bytes */
     uint64_t kernels;        /* kernels launched by this library */
     uint64_t host_driven;    /* queries run host-driven (requested or after an
