@@ -118,24 +118,30 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                smax.append(float(p[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, p[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clocks(self.lines)
+
+
+def summarize_clocks(lines) -> dict | None:
+    """Median SM clock, max clock and the throttle reasons seen in
+    nvidia-smi CSV lines (ClockSampler.FIELDS order, no header)."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        p = [x.strip() for x in ln.split(",")]
+        if len(p) < 9:
+            continue
+        try:
+            sm.append(float(p[1].split()[0]))
+            smax.append(float(p[2].split()[0]))
+        except (ValueError, IndexError):
+            continue
+        for nm, v in zip(names, p[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 KERNEL_SOURCES = {"k_query": ("join.cu", "join_tile.cuh", "common.cuh", "scan.cuh", "internal.h"),
