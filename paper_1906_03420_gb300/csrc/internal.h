@@ -122,7 +122,8 @@ struct DStep {
     int32_t *out;                      // output table region
     uint64_t out_bytes;                // bytes of the output region
     uint64_t row_cap;                  // output rows allowed (0 = no limit)
-    uint64_t *S;                       // scratch region: F and part at the front, caps at the back
+    uint64_t *S;                       // scratch region: F and part at the front, the per-row
+                                       // bound records (start, then length | edge) at the back
     uint64_t S_words;
     int32_t t, count_only;
     // set on the device
@@ -134,7 +135,8 @@ struct DStep {
 // Grid-barrier and status words of one cooperative query launch.
 struct QueryCtl {
     unsigned bar_count, bar_gen;
-    unsigned fail;        // 1 scratch too small, 2 table overflow, 4 barrier wait gave up
+    unsigned fail;        // 1 scratch too small (or a sub-list too long for a bound record),
+                          // 2 table overflow, 4 barrier wait gave up
     unsigned pad;
     unsigned long long spin_limit;   // sleeps before a barrier wait gives up (0 = default)
 };

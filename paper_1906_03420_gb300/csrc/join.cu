@@ -1,10 +1,18 @@
-// One join iteration (Sec. V, Algs. 3-4) as three launches:
+// Join iterations (Sec. V, Algs. 3-4), in two forms.
 //
+// Host-sized (gsi_join_step, and the splitting path of the memory-bounded
+// driver): one iteration as three launches,
 //   1. scan   F[i] = sum_{r<i} (cap_r + W), where cap_r bounds row r's output
 //             (Alg. 4's preallocation bound), plus W "row slots" per row that
-//             pay for staging the row (load balancing, below).
-//   2. part   for every tile of NV consecutive slots, its first row.
+//             pay for staging the row (load balancing, below);
+//   2. part   for every tile of NV consecutive slots, its first row;
 //   3. join   the fused kernel: one CTA per tile of NV slots.
+//
+// Device-driven (k_query): the seed and every iteration of one query in one
+// cooperative launch, the same three phases separated by bounded grid
+// barriers, tiles taken from a counter.  Its bound scan also keeps each row's
+// shortest sub-list (start, length, linking edge), so the join tiles stage
+// rows without searching again.
 //
 // Output bound.  Every neighbour list N(v,l) is stored sorted by (label rank
 // of the neighbour, neighbour id), so the neighbours of v via l that carry
@@ -308,7 +316,7 @@ __global__ void k_barrier_selftest(QueryCtl *ctl, unsigned expect) {
     grid_barrier(ctl, expect);
 }
 
-int g_smem_set[64];
+std::once_flag g_join_attr_once[64];
 
 StepDev step_dev(const gsi_graph *g, const JoinStep &s) {
     StepDev d;
@@ -376,10 +384,13 @@ gsi_status launch_join(const gsi_graph *g, const int32_t *M, uint64_t R, const J
     size_t sm = join_smem(a.rmax, s.t, s.d);
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !g_smem_set[dev]) {
-        GSI_CUDA_TRY(cudaFuncSetAttribute(k_join<JOIN_NT, JOIN_VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024));
-        g_smem_set[dev] = 1;
+    if (dev >= 0 && dev < 64) {                 // once per device, safe across host threads
+        cudaError_t e = cudaSuccess;
+        std::call_once(g_join_attr_once[dev], [&e]() {
+            e = cudaFuncSetAttribute(k_join<JOIN_NT, JOIN_VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024);
+        });
+        GSI_CUDA_TRY(e);
     }
     if (sm > 200 * 1024) {
         set_error("join: shared memory need exceeds 200 KB");
