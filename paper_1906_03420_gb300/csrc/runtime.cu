@@ -606,12 +606,21 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     x.h_stage = t_pinned + PINNED_READ;
     x.h_stage_bytes = PINNED_STAGE;
     unsigned long long *d_counts = nullptr;
-    GSI_TRY(dalloc(x, (void **)&x.bitmaps, bm_words * 4));
-    GSI_TRY(dalloc(x, (void **)&d_counts, 8 * GSI_MAX_QUERY_VERTICES + 32));
-    x.d_scalars = d_counts + GSI_MAX_QUERY_VERTICES;
-    GSI_CUDA_TRY(cudaMemsetAsync(x.d_scalars, 0, 32, x.st));
+    gsi_status rc = dalloc(x, (void **)&x.bitmaps, bm_words * 4);
+    if (rc == GSI_OK) rc = dalloc(x, (void **)&d_counts, 8 * GSI_MAX_QUERY_VERTICES + 32);
+    if (rc == GSI_OK) {
+        x.d_scalars = d_counts + GSI_MAX_QUERY_VERTICES;
+        if (cudaMemsetAsync(x.d_scalars, 0, 32, x.st) != cudaSuccess) {
+            set_error("query: clearing the counters failed");
+            rc = GSI_ECUDA;
+        }
+    }
+    if (rc != GSI_OK) {                     // nothing was launched: release what was reserved
+        if (x.bitmaps) cudaFreeAsync(x.bitmaps, x.st);
+        if (d_counts) cudaFreeAsync(d_counts, x.st);
+        return rc;
+    }
 
-    gsi_status rc = GSI_OK;
     x.tm.begin(0);
     rc = launch_filter(g, qs, x.bitmaps, d_counts, x.st);
     x.tm.end();
