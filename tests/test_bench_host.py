@@ -60,3 +60,14 @@ def test_committed_traffic_records_are_well_formed(kernel, workload):
     assert rec["kernel"] == kernel and rec["workload"] == workload
     assert rec["dram_bytes_per_launch"] > 0 and rec["ratio_to_alg_bytes"] > 0
     assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+
+
+def test_cpu_baseline_reports_cores_and_one_thread():
+    import synth
+    g = synth.workload_graph("tiny")
+    qs = synth.queries("tiny")
+    for q in qs:
+        q.bound = 1.0                                        # every tiny query is in the sample
+    out = bench.cpu_baseline(qs, g)
+    assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
+    assert out["one_thread"]["value"] > 0 and out["one_thread"]["query"] in range(len(qs))
