@@ -1,0 +1,109 @@
+"""The medium and batched configurations at full size, in the launch
+configurations the benchmark times.
+
+- medium: R-MAT 2^20 vertices / 16M edges, 64 Zipf vertex labels, 8 edge
+  labels, 100 walk queries of 6..12 vertices, one at a time on the plain path.
+- batched: the same graph, 4,096 walk queries of 4..7 vertices as one
+  prepared batch replayed from its captured CUDA graph.
+
+Parity where the oracle finishes in seconds: exact counts and the
+order-independent fingerprints of the whole embedding sets on the oracle
+sample (medium) and on a seeded 256-query sample (batched).  Every other
+query is checked by properties: the admission bound, the definition on its
+first materialised rows, and (batched) equality with the plain path."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+ROW_SAMPLE = 50_000
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1906_03420_gb300 as p
+    p.load()
+    torch.cuda.init()
+    return p
+
+
+@pytest.fixture(scope="module")
+def medium(pkg):
+    g = synth.workload_graph("medium")
+    G = pkg.Graph.from_synth(g)
+    O = oracle.OracleGraph.from_synth(g)
+    a = np.minimum(g.src, g.dst).astype(np.int64)
+    b = np.maximum(g.src, g.dst).astype(np.int64)
+    key = a * g.n + b
+    order = np.argsort(key, kind="stable")
+    return g, G, O, key[order], g.elab[order]
+
+
+def check_rows(g, q, rows, keys, labs):
+    """Every row is an embedding (labels, injectivity, every query edge with
+    its label) and no row repeats."""
+    if rows.shape[0] == 0:
+        return
+    assert (g.vlab[rows] == np.asarray(q.vlab)[None, :]).all()
+    s = np.sort(rows, axis=1)
+    assert (s[:, 1:] != s[:, :-1]).all()
+    for e in range(len(q.src)):
+        u, v, lab = int(q.src[e]), int(q.dst[e]), int(q.elab[e])
+        a = np.minimum(rows[:, u], rows[:, v]).astype(np.int64)
+        b = np.maximum(rows[:, u], rows[:, v]).astype(np.int64)
+        k = a * g.n + b
+        idx = np.minimum(np.searchsorted(keys, k), keys.shape[0] - 1)
+        assert (keys[idx] == k).all() and (labs[idx] == lab).all()
+    assert np.unique(rows, axis=0).shape[0] == rows.shape[0]
+
+
+def oracle_sample(qs, n=8, max_bound=2e7):
+    return [i for i, q in enumerate(qs) if q.bound <= max_bound][:n]
+
+
+def test_medium_plain_path_full_size(pkg, medium):
+    g, G, O, keys, labs = medium
+    assert g.n == 1 << 20 and g.m == 16_000_000
+    qs = synth.queries("medium")
+    sample = set(oracle_sample(qs))
+    assert len(sample) == 8
+    for i, q in enumerate(qs):
+        r = G.query(q)
+        c = r.count
+        assert c <= q.bound * (1 + 1e-9) + 1
+        if i in sample:
+            want, fp = oracle.count(O, q)
+            assert c == want, i
+            rows = r.rows()
+            assert rows.shape[0] == c
+            assert oracle.fingerprint(rows) == (want, fp[1], fp[2]), i
+        else:
+            rows = r.rows(max_rows=ROW_SAMPLE)
+            assert rows.shape[0] == min(c, ROW_SAMPLE)
+            check_rows(g, q, rows, keys, labs)
+        r.close()
+
+
+def test_batched_prepared_batch_full_size(pkg, medium):
+    g, G, O, keys, labs = medium
+    qs = synth.queries("batched")
+    assert len(qs) == 4096
+    pb = pkg.PreparedBatch(G, qs)
+    assert list(pb.statuses) == [0] * len(qs)
+    res = pb.run()
+    counts = [r.count for r in res]
+    assert counts == [G.query(q, count_only=True).count for q in qs]     # every query: batch == plain path
+    rng = np.random.default_rng(2004)
+    for i in sorted(rng.choice(len(qs), 256, replace=False).tolist()):
+        want, fp = oracle.count(O, qs[i])
+        assert counts[i] == want, i
+        assert oracle.fingerprint(res[i].rows()) == (want, fp[1], fp[2]), i
+    for i in range(0, len(qs), 97):                                       # the definition on other queries
+        check_rows(g, qs[i], res[i].rows(max_rows=ROW_SAMPLE), keys, labs)
+    pb.close()
