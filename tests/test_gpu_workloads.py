@@ -107,3 +107,30 @@ def test_batched_prepared_batch_full_size(pkg, medium):
     for i in range(0, len(qs), 97):                                       # the definition on other queries
         check_rows(g, qs[i], res[i].rows(max_rows=ROW_SAMPLE), keys, labs)
     pb.close()
+
+
+def test_served_full_size(pkg):
+    """Served configuration: R-MAT 2^22 vertices / 64M edges, 128 Zipf vertex
+    labels, 8 edge labels; the first 256 queries of the arrival stream all
+    submitted to a continuous-batching server (2 slots, 40 GB budget, as the
+    benchmark).  Every result equals the plain path's; a seeded 32-query
+    sample equals the oracle (counts and full-set fingerprints)."""
+    g = synth.workload_graph("served")
+    assert g.n == 1 << 22 and g.m == 64_000_000
+    G = pkg.Graph.from_synth(g)
+    qs = synth.queries("served", 256)
+    S = pkg.Server(G, mem_budget=40 << 30, n_streams=2, max_batch=0)
+    tickets = [S.submit(q) for q in qs]
+    served = []
+    for t in tickets:
+        r, lat = S.poll(t, -1)
+        assert lat >= 0
+        served.append(r)
+    S.close()
+    assert [r.count for r in served] == [G.query(q, count_only=True).count for q in qs]
+    O = oracle.OracleGraph.from_synth(g)
+    rng = np.random.default_rng(2005)
+    for i in sorted(rng.choice(len(qs), 32, replace=False).tolist()):
+        want, fp = oracle.count(O, qs[i])
+        assert served[i].count == want, i
+        assert oracle.fingerprint(served[i].rows()) == (want, fp[1], fp[2]), i
