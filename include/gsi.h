@@ -331,7 +331,8 @@ void gsi_batch_destroy(gsi_batch *b);
 /* ---------------------------------------------------------------- served */
 typedef struct {
     uint64_t mem_budget;     /* bytes for intermediate tables, split evenly over
-                                the slots; 0 = 40% of the device's memory */
+                                the slots; 0 = half of the device's free
+                                memory at creation */
     int32_t n_streams;       /* slots: worker threads, each with its own stream
                                 (0 = 2) */
     uint64_t row_cap;        /* per query */
@@ -348,10 +349,15 @@ typedef struct {
 } gsi_server_opts;
 
 /*
- * A serving loop over a resident graph (continuous batching): each slot takes
- * every pending request, up to max_batch, as one batch and runs it on its own
- * stream within its memory share, so requests arriving while other batches
- * are on the GPU join the next free slot and slots overlap on the device.
+ * A serving loop over a resident graph (continuous batching, no counterpart
+ * in the paper): each slot takes every pending request, up to max_batch, as
+ * one batch and runs it on its own stream within its memory share, so
+ * requests arriving while other batches are on the GPU join the next free
+ * slot and slots overlap on the device.  With fewer than min_batch requests
+ * pending a slot runs them one at a time on the plain path.  Creation
+ * reserves each slot's batch workspace (its share of mem_budget) so that no
+ * request waits for it; if that fails, batches reserve their memory as they
+ * run.  The graph must outlive the server.
  */
 gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opts, gsi_server **out);
 /* Enqueue a query (copied).  *ticket identifies it in gsi_server_poll. */
@@ -364,7 +370,12 @@ gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, uint64_t *t
  */
 gsi_status gsi_server_poll(gsi_server *s, uint64_t ticket, int32_t timeout_ms, gsi_result **out,
                            double *latency_ms);
+/* Cancel a request that no slot has taken yet: its poll then returns
+ * GSI_ECANCELLED.  A request already running finishes normally. */
 gsi_status gsi_server_cancel(gsi_server *s, uint64_t ticket);
+/* Finish every request already submitted, then stop the slots; results
+ * already handed out by gsi_server_poll stay valid, results never polled are
+ * destroyed. */
 void gsi_server_destroy(gsi_server *s);
 
 /* ------------------------------------------------------------------ misc */
