@@ -141,3 +141,32 @@ def test_negative_query_label_rejected(pkg):
     with pytest.raises(pkg.GsiError) as e:
         pkg.plan_order(q, [1, 1], [1])
     assert e.value.status == pkg.GSI_EINVAL
+
+
+def test_header_constants_match_the_binding(pkg):
+    """Status codes, semantics values and fixed sizes in include/gsi.h agree
+    with the constants and struct layouts of the Python binding."""
+    import ctypes
+    import re
+    from paper_1906_03420_gb300 import gsi as b
+    text = open(os.path.join(ROOT, "include", "gsi.h")).read()
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(GSI_[A-Z_]+)\s*=\s*(\d+)", text))
+    for name in ("GSI_OK", "GSI_EINVAL", "GSI_ENOMEM", "GSI_ECAPPED", "GSI_ETIMEOUT", "GSI_ECANCELLED", "GSI_ECUDA",
+                 "GSI_EBUSY", "GSI_ISOMORPHISM", "GSI_HOMOMORPHISM"):
+        assert getattr(pkg, name) == enums[name], name
+    defines = dict((k, int(v)) for k, v in re.findall(r"#define\s+(GSI_[A-Z_]+)\s+(\d+)", text))
+    assert defines["GSI_MAX_QUERY_VERTICES"] == 32 and defines["GSI_SIG_WORDS"] == b.SIG_WORDS
+    # every struct the binding passes by pointer has the header's field order and types
+    fields = lambda name: [f[0] for f in getattr(b, name)._fields_]
+    assert fields("c_query_opts") == ["stream", "row_cap", "mem_budget", "count_only", "semantics", "order", "stats",
+                                      "host_driven"]
+    assert fields("c_batch_opts") == ["stream", "row_cap", "mem_budget", "count_only", "stats", "seeds_per_item",
+                                      "item_rows"]
+    assert fields("c_server_opts") == ["mem_budget", "n_streams", "row_cap", "count_only", "max_batch",
+                                       "seeds_per_item", "item_rows", "min_batch"]
+    for st, members in (("gsi_query_opts", fields("c_query_opts")), ("gsi_batch_opts", fields("c_batch_opts")),
+                        ("gsi_server_opts", fields("c_server_opts"))):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + st + ";", text).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        declared = re.findall(r"(\w+)\s*;", body)
+        assert declared == members, (st, declared)
