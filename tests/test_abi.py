@@ -165,8 +165,17 @@ def test_header_constants_match_the_binding(pkg):
     assert fields("c_server_opts") == ["mem_budget", "n_streams", "row_cap", "count_only", "max_batch",
                                        "seeds_per_item", "item_rows", "min_batch"]
     for st, members in (("gsi_query_opts", fields("c_query_opts")), ("gsi_batch_opts", fields("c_batch_opts")),
-                        ("gsi_server_opts", fields("c_server_opts"))):
+                        ("gsi_server_opts", fields("c_server_opts")), ("gsi_graph_opts", fields("c_graph_opts")),
+                        ("gsi_graph_info", fields("c_graph_info")), ("gsi_stats", fields("c_stats")),
+                        ("gsi_query_desc", fields("c_query_desc"))):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + st + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-        declared = re.findall(r"(\w+)\s*;", body)
+        declared = []
+        for decl in body.split(";"):                    # "int32_t a, b" and "T *x[32]" forms
+            decl = re.sub(r"\[[^\]]*\]", "", decl).strip()
+            if not decl:
+                continue
+            names = decl.split(",")
+            declared.append(re.findall(r"(\w+)\s*$", names[0])[0])
+            declared += [n.strip().lstrip("*").strip() for n in names[1:]]
         assert declared == members, (st, declared)
