@@ -1,8 +1,9 @@
 """ORACLE -- test infrastructure only.
 
 Plain, slow CPU statement of the subgraph-isomorphism path (``oracle.c``):
-enumeration by definition (Defs. 1-3), brute force, the Sec. III-A signature
-filter and the result of one Alg. 3 join iteration.  Only ``tests/``,
+enumeration by definition (Defs. 1-3), brute force, homomorphism and edge
+isomorphism (Sec. VII-A), the Sec. III-A signature filter and the result of
+one Alg. 3 join iteration.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline / reference legs
 may import this package; the CUDA library never does, and the two share no
 code.  Built with gcc into ``liboracle.so`` by :func:`build`.
@@ -58,6 +59,10 @@ def _load():
         lib.oracle_enumerate_hom.restype = ctypes.c_int64
         lib.oracle_bruteforce_hom.argtypes = [vp] + q + [i32p, ctypes.c_int64]
         lib.oracle_bruteforce_hom.restype = ctypes.c_int64
+        lib.oracle_enumerate_edge.argtypes = [vp] + q + [i32p, ctypes.c_int64, ctypes.c_int32, u64p]
+        lib.oracle_enumerate_edge.restype = ctypes.c_int64
+        lib.oracle_bruteforce_edge.argtypes = [vp] + q + [i32p, ctypes.c_int64]
+        lib.oracle_bruteforce_edge.restype = ctypes.c_int64
         lib.oracle_murmur3_32.argtypes = [u8p, ctypes.c_int32, ctypes.c_uint32]
         lib.oracle_murmur3_32.restype = ctypes.c_uint32
         lib.oracle_data_signatures.argtypes = [vp, u32p]
@@ -171,6 +176,43 @@ def bruteforce_rows(g: OracleGraph, q, hom: bool = False) -> np.ndarray:
     if cnt < 0:
         raise ValueError("invalid query")
     out = np.empty((max(cnt, 1), k), np.int32)
+    fn(g._h, *a, _i32(out), cnt)
+    return sort_rows(out[:cnt])
+
+
+def enumerate_edge_rows(g: OracleGraph, q) -> np.ndarray:
+    """All edge-isomorphic matches (Sec. VII-A): rows of data edge ids, column
+    j = query edge j, sorted lexicographically."""
+    keep, a = _qargs(q)
+    fn = _load().oracle_enumerate_edge
+    cnt = fn(g._h, *a, None, 0, 1, None)
+    if cnt < 0:
+        raise ValueError("invalid query")
+    out = np.empty((max(cnt, 1), a[5]), np.int32)
+    fn(g._h, *a, _i32(out), cnt, 1, None)
+    return sort_rows(out[:cnt])
+
+
+def count_edge(g: OracleGraph, q, nthreads: int | None = None) -> tuple[int, tuple[int, int, int]]:
+    """(count, fingerprint) of the edge-isomorphic matches."""
+    keep, a = _qargs(q)
+    fp = (ctypes.c_uint64 * 3)()
+    nt = _threads() if nthreads is None else nthreads
+    cnt = _load().oracle_enumerate_edge(g._h, *a, None, 0, nt, fp)
+    if cnt < 0:
+        raise ValueError("invalid query")
+    return int(cnt), (int(fp[0]), int(fp[1]), int(fp[2]))
+
+
+def bruteforce_edge_rows(g: OracleGraph, q) -> np.ndarray:
+    """Edge-isomorphic matches by checking every map of query edges to data
+    edges (tiny inputs only)."""
+    keep, a = _qargs(q)
+    fn = _load().oracle_bruteforce_edge
+    cnt = fn(g._h, *a, None, 0)
+    if cnt < 0:
+        raise ValueError("invalid query")
+    out = np.empty((max(cnt, 1), a[5]), np.int32)
     fn(g._h, *a, _i32(out), cnt)
     return sort_rows(out[:cnt])
 

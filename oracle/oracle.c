@@ -18,6 +18,18 @@
  *                      Sec. VII-A: homomorphism semantics drops injectivity
  *                      (two query vertices may map to one data vertex); the
  *                      same backtracking and exhaustive check without it.
+ *   oracle_enumerate_edge, oracle_bruteforce_edge
+ *                      Sec. VII-A, edge isomorphism: all injective maps
+ *                      h: E(Q) -> E(G) such that h(e) has e's edge label and
+ *                      e's pair of endpoint labels, and any two query edges
+ *                      that share a query vertex b map to data edges that
+ *                      share a data vertex with b's label.  Computed on G
+ *                      itself (no line graph): backtracking over query edges,
+ *                      each after the first taken among the data edges
+ *                      incident to the image of an earlier adjacent edge;
+ *                      and the exhaustive check of all m^|E(Q)| maps.
+ *                      Rows hold data edge ids (positions in the caller's
+ *                      edge list), column j = query edge j.
  *   oracle_signature   Sec. III-A: N = 512-bit vertex signature.  The first
  *                      K = 32 bits hold the vertex label itself (Sec. VII-B
  *                      says single labels are stored directly); the other 480
@@ -33,7 +45,10 @@
  *
  * Readings where the paper is silent or garbled (the same list is kept in the
  * design notes): non-induced matching; mappings, not subgraphs; undirected
- * edges with one label per vertex pair; the signature hash is MurmurHash3
+ * edges with one label per vertex pair; edge isomorphism constrains only
+ * query edges that share a vertex (the method runs the non-induced matching
+ * on line graphs), and keeps edge labels, endpoint labels and the label of
+ * each shared vertex; the signature hash is MurmurHash3
  * x86_32 (the draft text names MurmurHash 2.0; the published text names no
  * hash) over the 8 little-endian bytes (L_e, L_v') with seed 0x9747B28C, and
  * group index = hash mod 240.
@@ -54,6 +69,9 @@ typedef struct {
     int64_t *start;   /* n+1 */
     int32_t *nbr;     /* 2m, ascending per vertex */
     int32_t *lab;     /* 2m */
+    int32_t *esrc, *edst, *elab;   /* m: the caller's edge list */
+    int32_t *inc;     /* 2m: ids of the edges at each vertex (same ranges as
+                         nbr), ascending */
 } og_t;
 
 static int cmp_i64(const void *a, const void *b) {
@@ -89,13 +107,30 @@ void *oracle_graph_new(int32_t n, int64_t m, const int32_t *vlab, const int32_t 
         for (int64_t i = a; i < b; ++i) { g->nbr[i] = (int32_t)(tmp[i - a] >> 32); g->lab[i] = (int32_t)(uint32_t)tmp[i - a]; }
     }
     free(tmp);
+    g->esrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    g->edst = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    g->elab = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    g->inc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    if (m > 0) {
+        memcpy(g->esrc, src, sizeof(int32_t) * (size_t)m);
+        memcpy(g->edst, dst, sizeof(int32_t) * (size_t)m);
+        memcpy(g->elab, elab, sizeof(int32_t) * (size_t)m);
+    }
+    cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    memcpy(cur, g->start, sizeof(int64_t) * (size_t)n);
+    for (int64_t e = 0; e < m; ++e) {      /* ascending e: each vertex's ids come out sorted */
+        g->inc[cur[src[e]]++] = (int32_t)e;
+        g->inc[cur[dst[e]]++] = (int32_t)e;
+    }
+    free(cur);
     return g;
 }
 
 void oracle_graph_free(void *p) {
     og_t *g = (og_t *)p;
     if (!g) return;
-    free(g->vlab); free(g->start); free(g->nbr); free(g->lab); free(g);
+    free(g->vlab); free(g->start); free(g->nbr); free(g->lab);
+    free(g->esrc); free(g->edst); free(g->elab); free(g->inc); free(g);
 }
 
 /* Label of edge {u, v} in G, or -1 if there is none. */
@@ -351,6 +386,228 @@ int64_t oracle_bruteforce(void *gp, int32_t k, const int32_t *qvlab, const int32
 int64_t oracle_bruteforce_hom(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
                               const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows) {
     return bruteforce_maps(gp, k, qvlab, qsrc, qdst, qelab, qm, out, max_rows, 0);
+}
+
+/* ------------------------------------------------- edge isomorphism (Sec. VII-A) */
+typedef struct {
+    int32_t qm;
+    int32_t a[32], b[32], lab[32];     /* query edge e = {a[e], b[e]}, label lab[e] */
+    int32_t la[32], lb[32];            /* endpoint labels of query edge e */
+} oqe_t;
+
+static int make_edge_query(oqe_t *q, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                           const int32_t *qelab, int32_t qm) {
+    oq_t chk;
+    if (qm < 1 || qm > 32) return -1;
+    if (make_query(&chk, k, qvlab, qsrc, qdst, qelab, qm)) return -1;   /* ids, loops, repeated pairs */
+    q->qm = qm;
+    for (int32_t e = 0; e < qm; ++e) {
+        q->a[e] = qsrc[e]; q->b[e] = qdst[e]; q->lab[e] = qelab[e];
+        q->la[e] = qvlab[qsrc[e]]; q->lb[e] = qvlab[qdst[e]];
+    }
+    return 0;
+}
+
+/* The query vertex edges e and f share, or -1. */
+static int32_t query_common(const oqe_t *q, int32_t e, int32_t f) {
+    if (e == f) return -1;
+    if (q->a[e] == q->a[f] || q->a[e] == q->b[f]) return q->a[e];
+    if (q->b[e] == q->a[f] || q->b[e] == q->b[f]) return q->b[e];
+    return -1;
+}
+
+/* The data vertex edges d and x share, or -1. */
+static int32_t data_common(const og_t *g, int32_t d, int32_t x) {
+    if (d == x) return -1;
+    if (g->esrc[d] == g->esrc[x] || g->esrc[d] == g->edst[x]) return g->esrc[d];
+    if (g->edst[d] == g->esrc[x] || g->edst[d] == g->edst[x]) return g->edst[d];
+    return -1;
+}
+
+/* Edge label and endpoint labels (as an unordered pair) of data edge d equal
+ * those of query edge e. */
+static int edge_labels_match(const og_t *g, const oqe_t *q, int32_t e, int32_t d) {
+    if (g->elab[d] != q->lab[e]) return 0;
+    int32_t x = g->vlab[g->esrc[d]], y = g->vlab[g->edst[d]];
+    return (x == q->la[e] && y == q->lb[e]) || (x == q->lb[e] && y == q->la[e]);
+}
+
+typedef struct {
+    const og_t *g;
+    const oqe_t *q;
+    int32_t order[32];          /* query edges in matching order (BFS over shared vertices) */
+    int32_t anchor[32];         /* an earlier position whose edge shares a vertex, -1 if none */
+} eplan_t;
+
+typedef struct {
+    const eplan_t *pl;
+    int32_t h[32];              /* h[p] = image of query edge order[p] */
+    int64_t count;
+    uint64_t fp_sum, fp_xor;
+    int32_t *out; int64_t max_rows;
+} estate_t;
+
+static void make_edge_plan(eplan_t *pl, const og_t *g, const oqe_t *q) {
+    pl->g = g; pl->q = q;
+    int32_t seen[32] = {0};
+    int32_t tail = 0;
+    for (int32_t root = 0; root < q->qm; ++root) {
+        if (seen[root]) continue;
+        int32_t head = tail;
+        pl->order[tail++] = root; seen[root] = 1;
+        while (head < tail) {
+            int32_t e = pl->order[head++];
+            for (int32_t f = 0; f < q->qm; ++f)
+                if (!seen[f] && query_common(q, e, f) >= 0) { seen[f] = 1; pl->order[tail++] = f; }
+        }
+    }
+    for (int32_t p = 0; p < q->qm; ++p) {
+        pl->anchor[p] = -1;
+        for (int32_t i = 0; i < p && pl->anchor[p] < 0; ++i)
+            if (query_common(q, pl->order[i], pl->order[p]) >= 0) pl->anchor[p] = i;
+    }
+}
+
+static int edge_feasible(const estate_t *s, int32_t p, int32_t d) {
+    const eplan_t *pl = s->pl;
+    const og_t *g = pl->g;
+    const oqe_t *q = pl->q;
+    int32_t e = pl->order[p];
+    if (!edge_labels_match(g, q, e, d)) return 0;
+    for (int32_t i = 0; i < p; ++i) {
+        if (s->h[i] == d) return 0;                                  /* injective */
+        int32_t b = query_common(q, pl->order[i], e);
+        if (b < 0) continue;                                         /* no constraint */
+        int32_t bl = b == q->a[e] ? q->la[e] : q->lb[e];             /* label of the shared query vertex */
+        int32_t x = data_common(g, s->h[i], d);
+        if (x < 0 || g->vlab[x] != bl) return 0;
+    }
+    return 1;
+}
+
+static void edge_emit(estate_t *s) {
+    const eplan_t *pl = s->pl;
+    int32_t row[32];
+    for (int32_t p = 0; p < pl->q->qm; ++p) row[pl->order[p]] = s->h[p];
+    uint64_t h = row_hash(row, pl->q->qm);
+    s->fp_sum += h; s->fp_xor ^= h;
+    if (s->out && s->count < s->max_rows)
+        memcpy(s->out + s->count * pl->q->qm, row, sizeof(int32_t) * (size_t)pl->q->qm);
+    s->count++;
+}
+
+static void edge_extend(estate_t *s, int32_t p) {
+    const eplan_t *pl = s->pl;
+    const og_t *g = pl->g;
+    if (p == pl->q->qm) { edge_emit(s); return; }
+    if (pl->anchor[p] < 0) {                 /* first edge of a component: every data edge */
+        for (int64_t d = 0; d < g->m; ++d)
+            if (edge_feasible(s, p, (int32_t)d)) { s->h[p] = (int32_t)d; edge_extend(s, p + 1); }
+        return;
+    }
+    /* the image shares a vertex with the anchor's image: an edge at one of its ends */
+    int32_t an = s->h[pl->anchor[p]];
+    int32_t ends[2] = {g->esrc[an], g->edst[an]};
+    for (int j = 0; j < 2; ++j)
+        for (int64_t i = g->start[ends[j]]; i < g->start[ends[j] + 1]; ++i) {
+            int32_t d = g->inc[i];
+            if (j == 1 && (g->esrc[d] == ends[0] || g->edst[d] == ends[0])) continue;   /* listed at ends[0] */
+            if (edge_feasible(s, p, d)) { s->h[p] = d; edge_extend(s, p + 1); }
+        }
+}
+
+typedef struct {
+    estate_t st;
+    int64_t *next;
+} eworker_t;
+
+static void *edge_worker(void *arg) {
+    eworker_t *w = (eworker_t *)arg;
+    const og_t *g = w->st.pl->g;
+    for (;;) {
+        int64_t d = __atomic_fetch_add(w->next, 1, __ATOMIC_RELAXED);
+        if (d >= g->m) break;
+        if (edge_feasible(&w->st, 0, (int32_t)d)) { w->st.h[0] = (int32_t)d; edge_extend(&w->st, 1); }
+    }
+    return NULL;
+}
+
+/*
+ * All edge-isomorphic matches of Q in G (Sec. VII-A).  Returns the count, or
+ * -1 for an invalid query (no edge, more than 32 edges, bad ids, a loop or a
+ * repeated pair).  Rows (qm data edge ids each, column j = query edge j) go to
+ * out for the first max_rows matches when out != NULL and nthreads == 1.
+ * fp[0..2] receives (count, sum h, xor h).
+ */
+int64_t oracle_enumerate_edge(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                              const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows, int32_t nthreads,
+                              uint64_t *fp) {
+    const og_t *g = (const og_t *)gp;
+    oqe_t q;
+    if (make_edge_query(&q, k, qvlab, qsrc, qdst, qelab, qm)) return -1;
+    eplan_t pl;
+    make_edge_plan(&pl, g, &q);
+    int64_t count = 0; uint64_t s = 0, x = 0;
+    if (nthreads <= 1) {
+        estate_t st;
+        memset(&st, 0, sizeof st);
+        st.pl = &pl; st.out = out; st.max_rows = out ? max_rows : 0;
+        edge_extend(&st, 0);
+        count = st.count; s = st.fp_sum; x = st.fp_xor;
+    } else {
+        if (nthreads > 256) nthreads = 256;
+        pthread_t th[256];
+        eworker_t *ws = (eworker_t *)calloc((size_t)nthreads, sizeof(eworker_t));
+        int64_t next = 0;
+        for (int t = 0; t < nthreads; ++t) {
+            ws[t].st.pl = &pl; ws[t].next = &next;
+            pthread_create(&th[t], NULL, edge_worker, &ws[t]);
+        }
+        for (int t = 0; t < nthreads; ++t) {
+            pthread_join(th[t], NULL);
+            count += ws[t].st.count; s += ws[t].st.fp_sum; x ^= ws[t].st.fp_xor;
+        }
+        free(ws);
+    }
+    if (fp) { fp[0] = (uint64_t)count; fp[1] = s; fp[2] = x; }
+    return count;
+}
+
+/*
+ * Every map h: E(Q) -> E(G) (m^qm maps, lexicographic in (h(0), ..., h(qm-1)))
+ * checked against the edge-isomorphism definition pair by pair.  Tiny inputs
+ * only.
+ */
+int64_t oracle_bruteforce_edge(void *gp, int32_t k, const int32_t *qvlab, const int32_t *qsrc, const int32_t *qdst,
+                               const int32_t *qelab, int32_t qm, int32_t *out, int64_t max_rows) {
+    const og_t *g = (const og_t *)gp;
+    oqe_t q;
+    if (make_edge_query(&q, k, qvlab, qsrc, qdst, qelab, qm)) return -1;
+    if (g->m < qm) return 0;
+    int32_t h[32];
+    int64_t count = 0;
+    for (int32_t e = 0; e < qm; ++e) h[e] = 0;
+    for (;;) {
+        int ok = 1;
+        for (int32_t e = 0; e < qm && ok; ++e) if (!edge_labels_match(g, &q, e, h[e])) ok = 0;
+        for (int32_t e = 0; e < qm && ok; ++e)
+            for (int32_t f = e + 1; f < qm; ++f) {
+                if (h[e] == h[f]) { ok = 0; break; }
+                int32_t b = query_common(&q, e, f);
+                if (b < 0) continue;
+                int32_t x = data_common(g, h[e], h[f]);
+                if (x < 0 || g->vlab[x] != qvlab[b]) { ok = 0; break; }
+            }
+        if (ok) {
+            if (out && count < max_rows) memcpy(out + count * qm, h, sizeof(int32_t) * (size_t)qm);
+            ++count;
+        }
+        int32_t i = qm - 1;
+        while (i >= 0 && h[i] == g->m - 1) { h[i] = 0; --i; }
+        if (i < 0) break;
+        h[i]++;
+    }
+    return count;
 }
 
 /* ------------------------------------------------------------- signature */
