@@ -378,6 +378,93 @@ gsi_status gsi_server_cancel(gsi_server *s, uint64_t ticket);
  * destroyed. */
 void gsi_server_destroy(gsi_server *s);
 
+/* ------------------------------------------------------ edge isomorphism */
+/*
+ * Edge isomorphism (Sec. VII-A): maps h: E(Q) -> E(G), injective, such that
+ * two query edges that share a query vertex map to data edges that share a
+ * data vertex.  The library follows the paper's reduction.
+ *   - G becomes its line graph G': vertex i of G' is edge i of G, and two G'
+ *     vertices are adjacent when their edges meet at a vertex.
+ *   - Q becomes Q' the same way.
+ *   - Q' is matched in G' by the ordinary path (gsi_query_run semantics:
+ *     non-induced, so query edges that share no vertex are unconstrained).
+ *   - A match of Q' is read back as an edge map: row column j holds the data
+ *     edge id (position in the caller's edge list) of query edge j.
+ * Labels: h(e) must carry e's edge label and e's unordered pair of endpoint
+ * labels.  Where two query edges meet at vertex b, their images must meet at
+ * a data vertex with b's label.  In G' this becomes:
+ *   - a vertex's label is a dense id of the triple (edge label, lower
+ *     endpoint-label rank, higher rank), in sorted triple order, where a rank
+ *     is the label's index among G's sorted distinct vertex labels;
+ *   - an edge's label is the rank of the shared vertex's label.
+ * Query labels that G lacks become values nothing in G' carries (-1 for a
+ * Q' vertex, INT32_MAX for a Q' edge), so such queries have no matches.
+ * The transform runs on the host.  G' has |E(G)| vertices and
+ * sum_v deg(v)(deg(v)-1)/2 edges, so it suits graphs without very
+ * high-degree vertices.
+ */
+typedef struct gsi_edge_graph gsi_edge_graph;
+
+/* gsi_edge_graph_create flag: build the transform's tables only, with no
+   device graph and no CUDA call (gsi_edge_graph_line and gsi_edge_query_line
+   work; gsi_edge_query_run returns GSI_EINVAL). */
+#define GSI_EDGE_HOST_ONLY 1
+
+/*
+ * Check G, build its line graph on the host and load it on the device with
+ * gsi_graph_create (opts as there; flags 0 or GSI_EDGE_HOST_ONLY).  Arrays as
+ * for gsi_graph_create; G's arrays are copied and kept for the transform.
+ * Errors: GSI_EINVAL for n < 1, m < 1, m >= 2^31, an id outside [0,n), a
+ * self-loop, a negative edge label, a repeated vertex pair, more than 65535
+ * distinct label triples, or a line graph of 2^31 edges or more;
+ * gsi_graph_create's errors for the device build; GSI_ENOMEM when host memory
+ * runs out.  *out is set only on GSI_OK.
+ */
+gsi_status gsi_edge_graph_create(const int32_t *vlab, int32_t n, const int32_t *src, const int32_t *dst,
+                                 const int32_t *elab, int64_t m, const gsi_graph_opts *opts, int32_t flags,
+                                 gsi_edge_graph **out);
+void gsi_edge_graph_destroy(gsi_edge_graph *g);
+/*
+ * G' copied to host arrays (each may be NULL): lvlab int32[m] (vertex i =
+ * edge i of G), and the first min(cap, |E(G')|) edges in lsrc, ldst, lelab.
+ * Edges are listed vertex by vertex of G, then by pairs of incident edges in
+ * ascending id order (lsrc < ldst).  *ln = |V(G')| = m, *lm = |E(G')|
+ * (optional).
+ */
+gsi_status gsi_edge_graph_line(const gsi_edge_graph *g, int32_t *lvlab, int32_t *lsrc, int32_t *ldst,
+                               int32_t *lelab, int64_t cap, int32_t *ln, int64_t *lm);
+/*
+ * The device line graph G' as an ordinary gsi_graph, owned by g.  Do not
+ * destroy it.  It is valid until gsi_edge_graph_destroy; host-only graphs
+ * give NULL.  Queries transformed by gsi_edge_query_line can run on it
+ * through every call of this header (batches, prepared batches, servers).
+ */
+gsi_status gsi_edge_graph_device(const gsi_edge_graph *g, gsi_graph **line);
+/*
+ * Q' of a query against G's label tables (host only).  Q is validated as for
+ * gsi_query_run and needs 1 <= qm <= 32 edges.  Outputs (each may be NULL):
+ *   - lvlab int32[qm] (vertex j = query edge j);
+ *   - the first min(cap, |E(Q')|) edges in lsrc, ldst, lelab, in the order
+ *     of gsi_edge_graph_line;
+ *   - *lk = qm and *lqm = |E(Q')| (optional).
+ * |E(Q')| <= 496.
+ */
+gsi_status gsi_edge_query_line(const gsi_edge_graph *g, const int32_t *qvlab, int32_t k, const int32_t *qsrc,
+                               const int32_t *qdst, const int32_t *qelab, int32_t qm, int32_t *lvlab,
+                               int32_t *lsrc, int32_t *ldst, int32_t *lelab, int32_t cap, int32_t *lk,
+                               int32_t *lqm);
+/*
+ * All edge-isomorphic matches of Q in G: Q' matched in G' by gsi_query_run
+ * with opts.  opts->semantics must be GSI_ISOMORPHISM.  An opts->order
+ * lists query edge ids.  The result has qm columns (column j = data edge id
+ * of query edge j); count, row cap and copy behave as for gsi_query_run.
+ * Errors: those of gsi_edge_query_line and gsi_query_run; GSI_EINVAL for a
+ * host-only graph or another semantics.
+ */
+gsi_status gsi_edge_query_run(gsi_edge_graph *g, const int32_t *qvlab, int32_t k, const int32_t *qsrc,
+                              const int32_t *qdst, const int32_t *qelab, int32_t qm, const gsi_query_opts *opts,
+                              gsi_result **out);
+
 /* ------------------------------------------------------------------ misc */
 /*
  * Self-test of the library's bounded device waits (no counterpart in the

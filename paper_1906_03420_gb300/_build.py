@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsi.so")
-SOURCES = ["sort.cu", "graph.cu", "filter.cu", "join.cu", "runtime.cu", "api.cu", "serve.cu", "noalloc.cu", "batch.cu", "replay.cu"]
+SOURCES = ["sort.cu", "graph.cu", "filter.cu", "join.cu", "runtime.cu", "api.cu", "serve.cu", "noalloc.cu", "batch.cu", "replay.cu", "edge.cu"]
 HEADERS = ["common.cuh", "scan.cuh", "internal.h", "runtime.h", "join_tile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -18,6 +18,7 @@ from . import _build
 
 GSI_OK, GSI_EINVAL, GSI_ENOMEM, GSI_ECAPPED, GSI_ETIMEOUT, GSI_ECANCELLED, GSI_ECUDA, GSI_EBUSY = range(8)
 GSI_ISOMORPHISM, GSI_HOMOMORPHISM = 0, 1
+GSI_EDGE_HOST_ONLY = 1
 STATUS_NAMES = {0: "GSI_OK", 1: "GSI_EINVAL", 2: "GSI_ENOMEM", 3: "GSI_ECAPPED", 4: "GSI_ETIMEOUT",
                 5: "GSI_ECANCELLED", 6: "GSI_ECUDA", 7: "GSI_EBUSY"}
 MAX_QUERY_VERTICES = 32
@@ -29,6 +30,8 @@ EXPORTED = [
     "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_join_step_noalloc", "gsi_plan_order",
     "gsi_batch_run", "gsi_batch_autotune", "gsi_batch_prepare", "gsi_batch_replay", "gsi_batch_destroy", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
     "gsi_server_destroy", "gsi_last_error", "gsi_version", "gsi_selftest_wait_timeout",
+    "gsi_edge_graph_create", "gsi_edge_graph_destroy", "gsi_edge_graph_line", "gsi_edge_graph_device",
+    "gsi_edge_query_line", "gsi_edge_query_run",
 ]
 
 
@@ -171,6 +174,22 @@ def load(build_if_missing: bool = False):
     L.gsi_server_cancel.restype = st
     L.gsi_server_destroy.argtypes = [VP]
     L.gsi_server_destroy.restype = None
+    L.gsi_edge_graph_create.argtypes = [I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int64,
+                                        ctypes.POINTER(c_graph_opts), ctypes.c_int32, ctypes.POINTER(VP)]
+    L.gsi_edge_graph_create.restype = st
+    L.gsi_edge_graph_destroy.argtypes = [VP]
+    L.gsi_edge_graph_destroy.restype = None
+    L.gsi_edge_graph_line.argtypes = [VP, I32P, I32P, I32P, I32P, ctypes.c_int64, I32P,
+                                      ctypes.POINTER(ctypes.c_int64)]
+    L.gsi_edge_graph_line.restype = st
+    L.gsi_edge_graph_device.argtypes = [VP, ctypes.POINTER(VP)]
+    L.gsi_edge_graph_device.restype = st
+    L.gsi_edge_query_line.argtypes = [VP, I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, I32P, I32P, I32P,
+                                      I32P, ctypes.c_int32, I32P, I32P]
+    L.gsi_edge_query_line.restype = st
+    L.gsi_edge_query_run.argtypes = [VP, I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32,
+                                     ctypes.POINTER(c_query_opts), ctypes.POINTER(VP)]
+    L.gsi_edge_query_run.restype = st
     L.gsi_last_error.argtypes = []
     L.gsi_last_error.restype = ctypes.c_char_p
     L.gsi_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
@@ -287,12 +306,23 @@ class Graph:
     def from_synth(cls, g, device: int = 0, stream=None) -> "Graph":
         return cls(g.vlab, g.src, g.dst, g.elab, device, stream)
 
+    @classmethod
+    def _borrowed(cls, handle: int, device: int, owner) -> "Graph":
+        """A view of a graph that `owner` holds (not destroyed by close())."""
+        g = cls.__new__(cls)
+        g._h = handle
+        g._keep = None
+        g.device = device
+        g._owner = owner
+        return g
+
     def __del__(self):
         self.close()
 
     def close(self):
         if getattr(self, "_h", None):
-            load().gsi_graph_destroy(self._h)
+            if getattr(self, "_owner", None) is None:
+                load().gsi_graph_destroy(self._h)
             self._h = None
 
     @property
@@ -388,6 +418,97 @@ class Graph:
         for i in range(len(qas)):
             res.append(Result(outs[i]) if sts[i] == GSI_OK else GsiError(sts[i], "batched query failed"))
         return res
+
+
+class EdgeGraph:
+    """Edge isomorphism (Sec. VII-A) by the line-graph transform
+    (gsi_edge_graph_*): G's line graph G' on the device; queries are
+    transformed to Q' and matched in G'.  Result rows hold data edge ids
+    (positions in this graph's edge list), column j for query edge j."""
+
+    def __init__(self, vlab, src, dst, elab, device: int = 0, stream=None, host_only: bool = False):
+        L = load()
+        vl, s, d, e = _i32(vlab), _i32(src), _i32(dst), _i32(elab)
+        h = VP()
+        opts = c_graph_opts(device, _stream_handle(stream))
+        _check(L.gsi_edge_graph_create(_p32(vl), vl.shape[0], _p32(s), _p32(d), _p32(e), s.shape[0],
+                                       ctypes.byref(opts), GSI_EDGE_HOST_ONLY if host_only else 0, ctypes.byref(h)),
+               "gsi_edge_graph_create")
+        self._h = h.value
+        self.device = device
+        self.m = int(s.shape[0])
+
+    @classmethod
+    def from_synth(cls, g, device: int = 0, stream=None, host_only: bool = False) -> "EdgeGraph":
+        return cls(g.vlab, g.src, g.dst, g.elab, device, stream, host_only)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gsi_edge_graph_destroy(self._h)
+            self._h = None
+
+    def line_graph(self) -> tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+        """G' on the host: (vlab int32[m], src, dst, elab int32[|E(G')|])."""
+        L = load()
+        ln = ctypes.c_int32()
+        lm = ctypes.c_int64()
+        _check(L.gsi_edge_graph_line(self._h, None, None, None, None, 0, ctypes.byref(ln), ctypes.byref(lm)),
+               "gsi_edge_graph_line")
+        vl = np.zeros(max(ln.value, 1), np.int32)
+        s, d, e = (np.zeros(max(lm.value, 1), np.int32) for _ in range(3))
+        _check(L.gsi_edge_graph_line(self._h, _p32(vl), _p32(s), _p32(d), _p32(e), lm.value, None, None),
+               "gsi_edge_graph_line")
+        return vl[: ln.value], s[: lm.value], d[: lm.value], e[: lm.value]
+
+    def line_query(self, q) -> QueryArrays:
+        """Q' against this graph's label tables (host only)."""
+        qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+        L = load()
+        cap = 32 * 31 // 2
+        vl = np.zeros(max(qa.qm, 1), np.int32)
+        s, d, e = (np.zeros(cap, np.int32) for _ in range(3))
+        lk = ctypes.c_int32()
+        lqm = ctypes.c_int32()
+        _check(L.gsi_edge_query_line(self._h, _p32(qa.vlab), qa.k, _p32(qa.src), _p32(qa.dst), _p32(qa.elab), qa.qm,
+                                     _p32(vl), _p32(s), _p32(d), _p32(e), cap, ctypes.byref(lk), ctypes.byref(lqm)),
+               "gsi_edge_query_line")
+        return QueryArrays(vl[: lk.value].copy(), s[: lqm.value].copy(), d[: lqm.value].copy(),
+                           e[: lqm.value].copy())
+
+    def line(self) -> Graph:
+        """G' as a Graph view (owned by this object) for batches and servers of line queries."""
+        g = VP()
+        _check(load().gsi_edge_graph_device(self._h, ctypes.byref(g)), "gsi_edge_graph_device")
+        if not g.value:
+            raise GsiError(GSI_EINVAL, "host-only edge graph has no device line graph")
+        return Graph._borrowed(g.value, self.device, self)
+
+    def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
+              order=None, stats: c_stats | None = None, host_driven: bool = False) -> Result:
+        qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+        o = c_query_opts()
+        o.stream = _stream_handle(stream)
+        o.row_cap = row_cap
+        o.mem_budget = mem_budget
+        o.count_only = int(count_only)
+        o.host_driven = int(host_driven)
+        ordr = None
+        if order is not None:
+            ordr = _i32(order)
+            o.order = _p32(ordr)
+        if stats is not None:
+            o.stats = ctypes.pointer(stats)
+        h = VP()
+        _check(load().gsi_edge_query_run(self._h, _p32(qa.vlab), qa.k, _p32(qa.src), _p32(qa.dst), _p32(qa.elab),
+                                         qa.qm, ctypes.byref(o), ctypes.byref(h)), "gsi_edge_query_run")
+        return Result(h.value)
+
+    def batch(self, queries, **kw) -> list:
+        """Edge queries as one batch on the line graph (Graph.batch on the Q')."""
+        return self.line().batch([self.line_query(q) for q in queries], **kw)
 
 
 class PreparedBatch:

@@ -156,6 +156,7 @@ def test_header_constants_match_the_binding(pkg):
         assert getattr(pkg, name) == enums[name], name
     defines = dict((k, int(v)) for k, v in re.findall(r"#define\s+(GSI_[A-Z_]+)\s+(\d+)", text))
     assert defines["GSI_MAX_QUERY_VERTICES"] == 32 and defines["GSI_SIG_WORDS"] == b.SIG_WORDS
+    assert defines["GSI_EDGE_HOST_ONLY"] == pkg.GSI_EDGE_HOST_ONLY
     # every struct the binding passes by pointer has the header's field order and types
     fields = lambda name: [f[0] for f in getattr(b, name)._fields_]
     assert fields("c_query_opts") == ["stream", "row_cap", "mem_budget", "count_only", "semantics", "order", "stats",
