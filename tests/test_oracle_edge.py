@@ -27,7 +27,7 @@ def og(g):
 
 @pytest.mark.parametrize("block", range(6))
 def test_edge_backtracking_equals_bruteforce(block):
-    """600 random labelled cases: backtracking over query edges equals the
+    """Random labelled cases (566 run): backtracking over query edges equals the
     exhaustive check of all m^|E(Q)| maps, rows and fingerprints."""
     rng = np.random.default_rng(4000 + block)
     for case in range(100):
