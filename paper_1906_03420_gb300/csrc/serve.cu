@@ -299,6 +299,44 @@ struct gsi_server {
     std::vector<BatchWorkspace> ws;        // one per slot (empty when batching is off)
 };
 
+// The work of one slot's take: requests one by one on the plain path, or as
+// one batch.
+template <class Publish>
+static void serve_batch(gsi_server *s, cudaStream_t st, uint64_t share, size_t max_batch, size_t min_batch,
+                        BatchWorkspace &ws, std::vector<std::shared_ptr<gsi_server::Req>> &batch,
+                        std::vector<gsi_result *> &res, std::vector<gsi_status> &sts, Publish &publish) {
+    if (max_batch == 1 || batch.size() < min_batch) {
+        // too few requests to fill the GPU with (query, seed range) items:
+        // one query at a time on the plain path, every step on all SMs
+        for (size_t i = 0; i < batch.size(); ++i) {
+            gsi_query_opts o;
+            std::memset(&o, 0, sizeof o);
+            o.stream = st;
+            o.row_cap = s->opts.row_cap;
+            o.count_only = s->opts.count_only;
+            o.mem_budget = share;
+            sts[i] = run_query(s->g, batch[i]->q, o, &res[i]);
+            publish(i, i + 1);
+        }
+        return;
+    }
+    std::vector<BatchPlan> plans(batch.size());
+    for (size_t i = 0; i < batch.size(); ++i) plans[i].q = batch[i]->q;
+    gsi_batch_opts bo;
+    std::memset(&bo, 0, sizeof bo);
+    bo.stream = st;
+    bo.row_cap = s->opts.row_cap;
+    bo.mem_budget = share;
+    bo.count_only = s->opts.count_only;
+    bo.seeds_per_item = s->opts.seeds_per_item;
+    bo.item_rows = s->opts.item_rows;
+    gsi_status rc = batch_execute(s->g, plans, bo, res, sts, ws.arena ? &ws : nullptr);
+    if (rc != GSI_OK)
+        for (size_t i = 0; i < batch.size(); ++i)
+            if (sts[i] == GSI_OK && !res[i]) sts[i] = rc;
+    publish(0, batch.size());
+}
+
 // One slot: a worker thread with its own stream and an equal share of the
 // memory budget.  It takes every pending request (up to max_batch) as one
 // batch, so requests that arrived while other batches were on the GPU are
@@ -311,12 +349,12 @@ static void server_worker(gsi_server *s, int idx) {
     const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
     const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
     const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 16;
-    (void)share;
     // the slot's batch workspace, reserved by gsi_server_create (results are
     // gathered out of it, so it is reused at once)
     BatchWorkspace &ws = s->ws[idx];
     for (;;) {
         std::vector<std::shared_ptr<gsi_server::Req>> batch;
+        bool cancelled = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
@@ -326,17 +364,17 @@ static void server_worker(gsi_server *s, int idx) {
                 s->queue.pop_front();
                 if (r->cancelled) {
                     r->status = GSI_ECANCELLED;
+                    cancelled = true;
                     continue;
                 }
                 batch.push_back(r);
             }
         }
-        if (batch.empty()) {
-            s->cv_done.notify_all();
-            continue;
-        }
+        if (cancelled) s->cv_done.notify_all();     // their pollers need not wait for this batch
+        if (batch.empty()) continue;
         std::vector<gsi_result *> res(batch.size(), nullptr);
         std::vector<gsi_status> sts(batch.size(), GSI_OK);
+        size_t published = 0;                        // requests [0, published) have their outcome
         // hand results [lo, hi) to their requests
         auto publish = [&](size_t lo, size_t hi) {
             auto now = std::chrono::steady_clock::now();
@@ -351,52 +389,54 @@ static void server_worker(gsi_server *s, int idx) {
                     batch[i]->status = sts[i];
                     batch[i]->latency_ms = std::chrono::duration<double, std::milli>(now - batch[i]->t_submit).count();
                 }
+                published = hi;
             }
             s->cv_done.notify_all();
         };
-        if (max_batch == 1 || batch.size() < min_batch) {
-            // too few requests to fill the GPU with (query, seed range) items:
-            // one query at a time on the plain path, every step on all SMs
-            for (size_t i = 0; i < batch.size(); ++i) {
-                gsi_query_opts o;
-                std::memset(&o, 0, sizeof o);
-                o.stream = st;
-                o.row_cap = s->opts.row_cap;
-                o.count_only = s->opts.count_only;
-                o.mem_budget = share;
-                sts[i] = run_query(s->g, batch[i]->q, o, &res[i]);
-                publish(i, i + 1);
+        try {
+            serve_batch(s, st, share, max_batch, min_batch, ws, batch, res, sts, publish);
+        } catch (...) {
+            // a host exception (allocation) must not leave the thread: the
+            // requests not yet answered fail, and results made for them are freed
+            gsi_status fail = GSI_ECUDA;
+            try {
+                throw;
+            } catch (const std::bad_alloc &) {
+                fail = GSI_ENOMEM;
+            } catch (...) {
             }
-            continue;
+            res.resize(batch.size(), nullptr);
+            sts.resize(batch.size(), fail);
+            for (size_t i = published; i < batch.size(); ++i) {
+                if (res[i]) gsi_result_destroy(res[i]);
+                res[i] = nullptr;
+                sts[i] = fail;
+            }
+            publish(published, batch.size());
         }
-        std::vector<BatchPlan> plans(batch.size());
-        for (size_t i = 0; i < batch.size(); ++i) plans[i].q = batch[i]->q;
-        gsi_batch_opts bo;
-        std::memset(&bo, 0, sizeof bo);
-        bo.stream = st;
-        bo.row_cap = s->opts.row_cap;
-        bo.mem_budget = share;
-        bo.count_only = s->opts.count_only;
-        bo.seeds_per_item = s->opts.seeds_per_item;
-        bo.item_rows = s->opts.item_rows;
-        gsi_status rc = batch_execute(s->g, plans, bo, res, sts, ws.arena ? &ws : nullptr);
-        if (rc != GSI_OK)
-            for (size_t i = 0; i < batch.size(); ++i)
-                if (sts[i] == GSI_OK && !res[i]) sts[i] = rc;
-        publish(0, batch.size());
     }
 }
 
-extern "C" gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opts, gsi_server **out) {
-    if (!g || !out) {
-        set_error("gsi_server_create: null argument");
-        return GSI_EINVAL;
+// Stop the slots after the queue drains, then release every resource the
+// server holds (also a partly created one).
+static void server_teardown(gsi_server *s) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
     }
-    GSI_TRY(prepare_device(g->device));
-    std::unique_ptr<gsi_server> s(new gsi_server());
-    s->g = g;
-    std::memset(&s->opts, 0, sizeof s->opts);
-    if (opts) s->opts = *opts;
+    s->cv_work.notify_all();
+    for (auto &w : s->workers) w.join();
+    for (auto &kv : s->all)
+        if (kv.second->res) gsi_result_destroy(kv.second->res);
+    for (auto st : s->streams) cudaStreamDestroy(st);
+    for (BatchWorkspace &w : s->ws) {
+        if (w.arena) cudaFree(w.arena);
+        if (w.result) cudaFree(w.result);
+    }
+    delete s;
+}
+
+static gsi_status server_start(gsi_server *s) {
     if (s->opts.n_streams < 1) s->opts.n_streams = 2;
     if (s->opts.mem_budget == 0) {
         size_t fr = 0, tot = 0;
@@ -423,8 +463,37 @@ extern "C" gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opt
             }
         }
     }
-    for (int i = 0; i < s->opts.n_streams; ++i) s->workers.emplace_back(server_worker, s.get(), i);
-    *out = s.release();
+    for (int i = 0; i < s->opts.n_streams; ++i) s->workers.emplace_back(server_worker, s, i);
+    return GSI_OK;
+}
+
+extern "C" gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opts, gsi_server **out) {
+    if (!g || !out) {
+        set_error("gsi_server_create: null argument");
+        return GSI_EINVAL;
+    }
+    *out = nullptr;
+    GSI_TRY(prepare_device(g->device));
+    gsi_server *s = nullptr;
+    gsi_status rc = GSI_ECUDA;
+    try {
+        s = new gsi_server();
+        s->g = g;
+        std::memset(&s->opts, 0, sizeof s->opts);
+        if (opts) s->opts = *opts;
+        rc = server_start(s);
+    } catch (const std::bad_alloc &) {
+        set_error("gsi_server_create: host allocation failed");
+        rc = GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_server_create: could not start the worker threads");
+        rc = GSI_ECUDA;
+    }
+    if (rc != GSI_OK) {
+        if (s) server_teardown(s);
+        return rc;
+    }
+    *out = s;
     return GSI_OK;
 }
 
@@ -491,19 +560,5 @@ extern "C" gsi_status gsi_server_cancel(gsi_server *s, uint64_t ticket) {
 }
 
 extern "C" void gsi_server_destroy(gsi_server *s) {
-    if (!s) return;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->stop = true;
-    }
-    s->cv_work.notify_all();
-    for (auto &w : s->workers) w.join();
-    for (auto &kv : s->all)
-        if (kv.second->res) gsi_result_destroy(kv.second->res);
-    for (auto st : s->streams) cudaStreamDestroy(st);
-    for (BatchWorkspace &w : s->ws) {
-        if (w.arena) cudaFree(w.arena);
-        if (w.result) cudaFree(w.result);
-    }
-    delete s;
+    if (s) server_teardown(s);
 }
