@@ -111,6 +111,9 @@ extern "C" gsi_status gsi_batch_prepare(gsi_graph *g, const gsi_query_desc *qs, 
     } catch (const std::bad_alloc &) {
         set_error("gsi_batch_prepare: host allocation failed");
         return GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_batch_prepare: unexpected host exception");
+        return GSI_ECUDA;
     }
 }
 
@@ -169,6 +172,9 @@ extern "C" gsi_status gsi_batch_replay(gsi_batch *b, gsi_result **outs, int32_t 
     } catch (const std::bad_alloc &) {
         set_error("gsi_batch_replay: host allocation failed");
         return GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_batch_replay: unexpected host exception");
+        return GSI_ECUDA;
     }
 }
 

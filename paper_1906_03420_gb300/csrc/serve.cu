@@ -214,6 +214,9 @@ extern "C" gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int3
     } catch (const std::bad_alloc &) {
         set_error("gsi_batch_run: host allocation failed");
         return GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_batch_run: unexpected host exception");
+        return GSI_ECUDA;
     }
 }
 
@@ -272,6 +275,9 @@ extern "C" gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs,
     } catch (const std::bad_alloc &) {
         set_error("gsi_batch_autotune: host allocation failed");
         return GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_batch_autotune: unexpected host exception");
+        return GSI_ECUDA;
     }
 }
 
@@ -502,18 +508,26 @@ extern "C" gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, 
         set_error("gsi_server_submit: null argument");
         return GSI_EINVAL;
     }
-    auto r = std::make_shared<gsi_server::Req>();
-    GSI_TRY(validate_query(q->vlab, q->k, q->src, q->dst, q->elab, q->qm, &r->q));
-    r->t_submit = std::chrono::steady_clock::now();
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        r->ticket = s->next_ticket++;
-        s->all[r->ticket] = r;
-        s->queue.push_back(r);
+    try {
+        auto r = std::make_shared<gsi_server::Req>();
+        GSI_TRY(validate_query(q->vlab, q->k, q->src, q->dst, q->elab, q->qm, &r->q));
+        r->t_submit = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->all[s->next_ticket] = r;              // may throw: the ticket is taken only after
+            s->queue.push_back(r);
+            r->ticket = s->next_ticket++;
+        }
+        s->cv_work.notify_one();
+        *ticket = r->ticket;
+        return GSI_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("gsi_server_submit: host allocation failed");
+        return GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_server_submit: unexpected host exception");
+        return GSI_ECUDA;
     }
-    s->cv_work.notify_one();
-    *ticket = r->ticket;
-    return GSI_OK;
 }
 
 extern "C" gsi_status gsi_server_poll(gsi_server *s, uint64_t ticket, int32_t timeout_ms, gsi_result **out,
