@@ -153,7 +153,7 @@ def falling(x, k):
 
 
 def worked_example():
-    """(printed facts, graph, query) of the Sec. IV worked example fixture."""
+    """(printed facts, graph, query) of the worked-example fixture (Secs. III-B, IV, V)."""
     import os
     facts, vl, E, qvl, QE = {}, None, [], None, []
     path = os.path.join(os.path.dirname(__file__), "golden", "worked_example.txt")

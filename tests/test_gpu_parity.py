@@ -415,7 +415,7 @@ def test_relabelling_invariance(pkg):
 
 
 def test_worked_example_on_gpu(pkg):
-    """The Sec. IV worked example (tests/golden): one join step from
+    """The worked example of Secs. III-B and V (tests/golden): one join step from
     M = {(v0, v_i)} leaves (v0, v100, v201); the full query finds the single
     printed match."""
     facts, g, q = H.worked_example()

@@ -343,9 +343,9 @@ def test_homomorphism_closed_forms():
         assert oracle.count(G, c4, hom=True)[0] == int(np.trace(np.linalg.matrix_power(A, 4)))
 
 
-# ------------------------------------------------------- worked example (Sec. IV)
+# ------------------------------------------- worked example (Secs. III-B, IV, V)
 def test_worked_example_fixture_holds_the_printed_facts():
-    """The constructed graph satisfies every Prealloc fact Sec. IV-C prints."""
+    """The constructed graph satisfies every Prealloc fact Sec. V prints."""
     facts, g, q = H.worked_example()
     G = og(g)
     nbr = lambda v, l: sorted(w for w in range(g.n) if w != v and G.edge_label(v, w) == l)
@@ -356,6 +356,27 @@ def test_worked_example_fixture_holds_the_printed_facts():
     assert sum(caps_a[:99]) == facts["buf99_offset"][0] and caps_a[99] == facts["num_L99_a"][0]
     assert sum(caps_b) == facts["gba_u0u2"][0]
     assert [w for w in nbr(100, 0) if w not in (0, 100)] == facts["buf99_subtracted"]
+
+
+def test_worked_example_fixture_holds_the_other_printed_facts():
+    """Facts printed about the same graph outside the Prealloc example:
+    - Sec. III-B's candidate sets are the vertex-label classes.  The
+      signature filter keeps a subset of each (a reading: the text lists
+      candidates by label);
+    - Sec. IV's P(G,b) has two edges, on v0, v1, v101 and v201;
+    - Sec. IV's PCSR example gives N(v0,a) 100 entries."""
+    facts, g, q = H.worked_example()
+    G = og(g)
+    member, _ = oracle.filter_sets(G, q)
+    for u in range(q.k):
+        lo, hi = facts[f"cand_u{u}"]
+        printed = list(range(lo, hi + 1))
+        assert np.flatnonzero(g.vlab == q.vlab[u]).tolist() == printed
+        assert set(np.flatnonzero(member[u]).tolist()) <= set(printed)
+    b = g.elab == 1
+    assert int(b.sum()) == facts["pgb_edges"][0]
+    assert sorted(set(g.src[b].tolist()) | set(g.dst[b].tolist())) == facts["pgb_vertices"]
+    assert sum(G.edge_label(0, w) == 0 for w in range(g.n)) == facts["n_v0_a"][0]
 
 
 def test_worked_example_oracle_join_and_match():
