@@ -5,8 +5,7 @@ owns all device memory, a serving path that must not wait on an allocator, a
 process under a strict memory quota).  They call gsi_join_step_noalloc, whose
 scratch is one static device array.  This file checks, through the C ABI,
 that two calls in a row give the same result as the allocating entry point,
-and that sizes beyond the array's limits are rejected.  It is collected last
-so that a failure here does not hide any other test's result.
+and that sizes beyond the array's limits are rejected.
 """
 import numpy as np
 import pytest
