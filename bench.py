@@ -192,13 +192,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     if args.queries:
         queries = [queries[i] for i in parse_query_list(args.queries, len(queries))]
     mine = shard(queries, rank, world)
-    G = pkg.Graph.from_synth(g, device=local_rank)
+    edge = args.workload == "edge"                  # edge isomorphism: queries matched in the line graph
+    G = (pkg.EdgeGraph if edge else pkg.Graph).from_synth(g, device=local_rank)
+    cols = (lambda q: len(q.src)) if edge else (lambda q: q.k)      # result columns of a query
+    unit = "edge matches/s" if edge else "embeddings/s"
     stream = torch.cuda.Stream()                    # every launch of the step goes to this stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     row_cap = w.row_cap
     budget = int(args.budget_gb * (1 << 30))
 
-    batched = args.mode == "batched" or (args.mode == "auto" and args.workload == "batched")
+    batched = not edge and (args.mode == "batched" or (args.mode == "auto" and args.workload == "batched"))
 
     def plain_step(stats_list=None):
         total = 0
@@ -303,7 +306,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         counts = []
         for q in mine:
             r = G.query(q, stream=stream, row_cap=row_cap, count_only=True)
-            counts.append((r.count, q.k))
+            counts.append((r.count, cols(q)))
             r.close()
         max_bytes = max([min(c, row_cap or c) * k * 4 for c, k in counts] + [4])
         host = _t.empty(max_bytes // 4 + 1, dtype=_t.int32, pin_memory=True)
@@ -319,7 +322,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                 for q, r in zip(mine, res):
                     c = r.count
                     rows, _capped = r.copy_to(host.data_ptr(), c)
-                    d2h += rows * q.k * 4 + 8
+                    d2h += rows * cols(q) * 4 + 8
                     emb += c
                     r.close()
                 continue
@@ -327,12 +330,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                 r = G.query(q, stream=stream, row_cap=row_cap)
                 c = r.count
                 rows, _capped = r.copy_to(host.data_ptr(), c)
-                d2h += rows * q.k * 4 + 8
+                d2h += rows * cols(q) * 4 + 8
                 emb += c
                 r.close()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        e2e = {"value": emb / el if el > 0 else None, "unit": "embeddings/s",
+        e2e = {"value": emb / el if el > 0 else None, "unit": unit,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // args.e2e_steps),
                "steps": args.e2e_steps, "ms_per_step": el * 1e3 / args.e2e_steps,
                "queries_per_s": len(mine) * args.e2e_steps / el if el > 0 else None}
@@ -361,10 +364,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
            "materialised": True, "parallelism": f"queries sharded over {world} GPU(s)",
            "launch": ("one prepared batch per step, replayed from a captured CUDA graph (filter + batch kernel)"
                       if batched else "one query at a time (filter + one cooperative join launch)")}
+    if edge:
+        li = G.line().info()
+        cfg["semantics"] = ("edge isomorphism (Sec. VII-A): G's line graph resident on the device, each query's "
+                            "line graph transformed on the host and matched in it")
+        cfg["line_graph"] = {"vertices": int(li.n), "edges": int(li.m)}
     out = {"metric": METRIC, "value": tot_emb / (t_max_ms * 1e-3) if t_max_ms > 0 else None,
-           "unit": "embeddings/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": t_max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded R-MAT graph, random-walk queries)",
+           "vs_baseline": None, "dtype": "int32", "data": data_desc(args.workload),
            "config": cfg, "queries_per_s": tot_q / (t_max_ms * 1e-3) if t_max_ms > 0 else None,
            "embeddings_per_step": tot_emb / args.steps, "wall_s": wall, "roofline": roofline,
            "filter": {"achieved_gbs": fb / (fms * 1e-3) / 1e9 if fms > 0 else None, "ms_per_step": fms / args.steps},
@@ -375,35 +383,43 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     if plain_cmp is not None:
         out["plain_path_same_queries"] = plain_cmp
     if args.cpu_baseline and rank == 0:
-        out["cpu_baseline"] = cpu_baseline(queries, g)
+        out["cpu_baseline"] = cpu_baseline(queries, g, edge=edge)
     return out
 
 
-def cpu_baseline(queries, g) -> dict:
+def data_desc(workload: str) -> str:
+    kind = "Erdos-Renyi" if workload in ("tiny", "edge") else "R-MAT"
+    return f"synthetic (seeded {kind} graph, random-walk queries)"
+
+
+def cpu_baseline(queries, g, edge: bool = False) -> dict:
     """The oracle on all host cores over the fixed sample, plus one thread on
-    the sample's quickest query (the parallel speed-up in context)."""
+    the sample's quickest query (the parallel speed-up in context).  With
+    edge=True the oracle counts edge-isomorphic matches on G itself."""
     import oracle
     O = oracle.OracleGraph.from_synth(g)
+    count = oracle.count_edge if edge else oracle.count
+    unit = "edge matches/s" if edge else "embeddings/s"
     idx = cpu_sample(queries)
     emb = 0
     per = []
     t0 = time.perf_counter()
     for i in idx:
         ta = time.perf_counter()
-        c = oracle.count(O, queries[i])[0]
+        c = count(O, queries[i])[0]
         per.append((time.perf_counter() - ta, c, i))
         emb += c
     el = time.perf_counter() - t0
-    out = {"value": emb / el if el > 0 else None, "unit": "embeddings/s", "cores": _threads(), "kind": "oracle",
+    out = {"value": emb / el if el > 0 else None, "unit": unit, "cores": _threads(), "kind": "oracle",
            "sample": f"queries {idx} of the workload (first 8 with admission bound <= 2e7), "
-                     f"{emb} embeddings enumerated in {el:.1f} s"}
+                     f"{emb} {'edge matches' if edge else 'embeddings'} enumerated in {el:.1f} s"}
     timed = [p for p in per if p[1] > 0]
     if timed:
         t_all, c, i = min(timed)
         ta = time.perf_counter()
-        oracle.count(O, queries[i], nthreads=1)
+        count(O, queries[i], nthreads=1)
         t1 = time.perf_counter() - ta
-        out["one_thread"] = {"value": c / t1 if t1 > 0 else None, "unit": "embeddings/s", "query": i,
+        out["one_thread"] = {"value": c / t1 if t1 > 0 else None, "unit": unit, "query": i,
                              "seconds": t1, "all_cores_seconds": t_all}
     return out
 
@@ -521,9 +537,12 @@ def run_reference(args) -> dict:
     O = oracle.OracleGraph.from_synth(g)
     idx = cpu_sample(queries)
     sample = [queries[i] for i in idx]
+    edge = args.workload == "edge"
+    count = oracle.count_edge if edge else oracle.count
+    unit = "edge matches/s" if edge else "embeddings/s"
 
     def step():
-        return sum(oracle.count(O, q)[0] for q in sample)
+        return sum(count(O, q)[0] for q in sample)
 
     for _ in range(args.warmup):
         step()
@@ -538,14 +557,16 @@ def run_reference(args) -> dict:
            "queries": w.n_queries, "k_range": [w.k_lo, w.k_hi], "query_admission_bound": w.max_bound,
            "materialised": False, "sample": idx}
     desc = f"queries {idx} (first 8 with admission bound <= 2e7) per step, count + fingerprint enumeration"
-    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "embeddings/s", "n_gpus": 0,
+    if edge:
+        cfg["semantics"] = "edge isomorphism (Sec. VII-A), counted by the oracle on G itself"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic (seeded R-MAT graph, random-walk queries)", "config": cfg,
+            "data": data_desc(args.workload), "config": cfg,
             "queries_per_s": len(sample) * args.steps / el if el > 0 else None,
-            "cpu_baseline": {"value": value, "unit": "embeddings/s", "cores": _threads(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": _threads(), "kind": "oracle",
                              "sample": desc},
-            "e2e": {"value": value, "unit": "embeddings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():

@@ -23,6 +23,13 @@ Workload recipes (``workload(name)``) fix every seed:
 * ``served``   R-MAT scale 22, 64M edges, 128 Zipf vertex labels, 8 edge
                labels; 20,000 queries, k = 4 + Geometric(mean 2) clipped to
                [4, 7], Poisson arrivals.
+* ``edge``     Erdos-Renyi n=2^20, m=4M (degree at most a few dozen, so its
+               line graph stays small: 4M vertices, about 30M edges); 4
+               uniform vertex labels, 2 uniform edge labels; 100 random-walk
+               queries with k ~ U{4..8}, asked as edge-isomorphism queries
+               (Sec. VII-A).  The admission bound counts vertex
+               homomorphisms, which bound the edge matches only roughly
+               (they run 1-4x the embeddings here).
 
 Random walks on these R-MAT graphs often hit hubs, and with only 8-16 edge
 labels a tree-shaped walk query can have 10^9-10^13 embeddings.  Each walk
@@ -279,6 +286,7 @@ GRAPHS = {
     "rmat20": GraphSpec("rmat", 1 << 20, 16_000_000, 64, 8, "zipf", 1002, scale=20),
     "rmat24": GraphSpec("rmat", 1 << 24, 256_000_000, 256, 16, "zipf", 1003, scale=24),
     "rmat22": GraphSpec("rmat", 1 << 22, 64_000_000, 128, 8, "zipf", 1005, scale=22),
+    "er20": GraphSpec("er", 1 << 20, 4_000_000, 4, 2, "uniform", 1006),
 }
 
 WORKLOADS = {
@@ -293,6 +301,9 @@ WORKLOADS = {
                             description="R-MAT 2^20 graph, 4096 walk queries k=4..16"),
     "served": WorkloadSpec("served", GRAPHS["rmat22"], 20000, 4, 7, "geometric", 2005, max_bound=1e6,
                            description="R-MAT 2^22 / 64M edges, 20000 walk queries k=4+Geom (mean 8)"),
+    "edge": WorkloadSpec("edge", GRAPHS["er20"], 100, 4, 8, "uniform", 2006, max_bound=1e7,
+                         description="ER 2^20 / 4M edges, 4 vlabels, 2 elabels, 100 walk queries k=4..8 "
+                                     "asked as edge-isomorphism queries"),
 }
 
 _GRAPH_CACHE: dict[str, Graph] = {}

@@ -4,6 +4,7 @@ records keyed by kernel source hashes."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
@@ -71,3 +72,34 @@ def test_cpu_baseline_reports_cores_and_one_thread():
     out = bench.cpu_baseline(qs, g)
     assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
     assert out["one_thread"]["value"] > 0 and out["one_thread"]["query"] in range(len(qs))
+
+
+def test_cpu_baseline_edge_mode_counts_edge_matches():
+    """With edge=True the baseline counts the oracle's edge-isomorphic matches."""
+    import oracle
+    import synth
+    g = synth.workload_graph("tiny")
+    qs = synth.queries("tiny")
+    for q in qs:
+        q.bound = 1.0
+    out = bench.cpu_baseline(qs, g, edge=True)
+    assert out["unit"] == "edge matches/s" and out["value"] > 0
+    O = oracle.OracleGraph.from_synth(g)
+    total = sum(oracle.count_edge(O, q)[0] for q in qs)
+    assert f"{total} edge matches" in out["sample"]
+
+
+def test_edge_workload_recipe():
+    """The edge workload's graph has bounded degree (its line graph stays
+    within the transform's 2^31-edge limit) and its queries are connected
+    walks with at least one edge."""
+    import synth
+    w = synth.WORKLOADS["edge"]
+    assert w.graph.kind == "er" and w.graph.n == 1 << 20 and w.graph.m == 4_000_000
+    assert bench.data_desc("edge") == "synthetic (seeded Erdos-Renyi graph, random-walk queries)"
+    assert bench.data_desc("medium") == "synthetic (seeded R-MAT graph, random-walk queries)"
+    g = synth.workload_graph("edge")
+    deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).astype(np.int64)
+    assert int((deg * (deg - 1) // 2).sum()) < 2 ** 31
+    qs = synth.queries("edge", 4)
+    assert all(1 <= len(q.src) <= 32 and w.k_lo <= q.k <= w.k_hi for q in qs)

@@ -188,3 +188,22 @@ def test_device_edge_graph_needs_a_gpu(pkg):
     with pytest.raises(pkg.GsiError) as e:
         pkg.EdgeGraph(g.vlab, g.src, g.dst, g.elab)
     assert e.value.status == pkg.GSI_ECUDA
+
+
+def test_transform_at_the_benchmark_size(pkg):
+    """The edge workload's full graph (ER 2^20 / 4M edges; line graph 4M
+    vertices, about 30.5M edges): the library's G' and Q' of the first three
+    queries, matched by the oracle's vertex enumeration, give exactly the
+    oracle's edge matches on G (rows and fingerprints)."""
+    import synth
+    g = synth.workload_graph("edge")
+    eg = pkg.EdgeGraph.from_synth(g, host_only=True)
+    vl, s, d, e = eg.line_graph()
+    deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).astype(np.int64)
+    assert vl.shape[0] == g.m and s.shape[0] == int((deg * (deg - 1) // 2).sum())
+    lg = og(vl, s, d, e)
+    O = og(g.vlab, g.src, g.dst, g.elab)
+    for i, q in enumerate(synth.queries("edge", 3)):
+        got = oracle.enumerate_rows(lg, eg.line_query(q))
+        want, fp = oracle.count_edge(O, q)
+        assert got.shape[0] == want and oracle.fingerprint(got) == (want, fp[1], fp[2]), i

@@ -110,3 +110,22 @@ def test_edge_query_semantics_and_row_cap(pkg):
     rc = pkg.load().gsi_edge_query_run(E._h, pkg.gsi._p32(q.vlab), q.k, pkg.gsi._p32(q.src), pkg.gsi._p32(q.dst),
                                        pkg.gsi._p32(q.elab), q.qm, ctypes.byref(o), ctypes.byref(h))
     assert rc == pkg.GSI_EINVAL
+
+
+def test_edge_workload_full_size(pkg):
+    """The edge workload the benchmark times: ER 2^20 / 4M edges (line graph
+    4M vertices, about 30.5M edges), 100 walk queries of 4..8 vertices asked
+    as edge-isomorphism queries, one at a time.  Every query's count and
+    full-set fingerprint equal the oracle's, which enumerates on G itself."""
+    g = synth.workload_graph("edge")
+    assert g.n == 1 << 20 and g.m == 4_000_000
+    E = pkg.EdgeGraph.from_synth(g)
+    O = og(g)
+    for i, q in enumerate(synth.queries("edge")):
+        want, fp = oracle.count_edge(O, q)
+        r = E.query(q)
+        assert r.count == want, i
+        rows = r.rows()
+        assert rows.shape == (want, len(q.src)), i
+        assert oracle.fingerprint(rows) == (want, fp[1], fp[2]), i
+        r.close()
