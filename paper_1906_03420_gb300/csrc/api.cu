@@ -42,22 +42,6 @@ gsi::ResultArena::~ResultArena() {
     if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }
 
-namespace {
-
-#define GSI_API_BEGIN try {
-#define GSI_API_END                                                                              \
-    }                                                                                            \
-    catch (const std::bad_alloc &) {                                                             \
-        set_error("host allocation failed");                                                    \
-        return GSI_ENOMEM;                                                                       \
-    }                                                                                            \
-    catch (...) {                                                                                \
-        set_error("unexpected host exception");                                                  \
-        return GSI_ECUDA;                                                                        \
-    }
-
-}  // namespace
-
 extern "C" {
 
 const char *gsi_version(void) { return "gsi-gb300 0.1 (sm_103a)"; }

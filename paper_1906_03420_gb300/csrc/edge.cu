@@ -45,18 +45,6 @@ struct gsi_edge_graph {
 
 namespace {
 
-#define EDGE_API_BEGIN try {
-#define EDGE_API_END                                                                             \
-    }                                                                                            \
-    catch (const std::bad_alloc &) {                                                             \
-        set_error("host allocation failed");                                                    \
-        return GSI_ENOMEM;                                                                       \
-    }                                                                                            \
-    catch (...) {                                                                                \
-        set_error("unexpected host exception");                                                  \
-        return GSI_ECUDA;                                                                        \
-    }
-
 int32_t rank_of(const std::vector<int32_t> &sorted, int32_t label) {
     auto it = std::lower_bound(sorted.begin(), sorted.end(), label);
     return (it != sorted.end() && *it == label) ? (int32_t)(it - sorted.begin()) : -1;
@@ -217,7 +205,7 @@ extern "C" {
 gsi_status gsi_edge_graph_create(const int32_t *vlab, int32_t n, const int32_t *src, const int32_t *dst,
                                  const int32_t *elab, int64_t m, const gsi_graph_opts *opts, int32_t flags,
                                  gsi_edge_graph **out) {
-    EDGE_API_BEGIN
+    GSI_API_BEGIN
     if (!out) {
         set_error("gsi_edge_graph_create: null out");
         return GSI_EINVAL;
@@ -252,7 +240,7 @@ gsi_status gsi_edge_graph_create(const int32_t *vlab, int32_t n, const int32_t *
     }
     *out = eg.release();
     return GSI_OK;
-    EDGE_API_END
+    GSI_API_END
 }
 
 void gsi_edge_graph_destroy(gsi_edge_graph *g) {
@@ -263,7 +251,7 @@ void gsi_edge_graph_destroy(gsi_edge_graph *g) {
 
 gsi_status gsi_edge_graph_line(const gsi_edge_graph *g, int32_t *lvlab, int32_t *lsrc, int32_t *ldst,
                                int32_t *lelab, int64_t cap, int32_t *ln, int64_t *lm) {
-    EDGE_API_BEGIN
+    GSI_API_BEGIN
     if (!g) {
         set_error("gsi_edge_graph_line: null graph");
         return GSI_EINVAL;
@@ -272,7 +260,7 @@ gsi_status gsi_edge_graph_line(const gsi_edge_graph *g, int32_t *lvlab, int32_t 
     if (lm) *lm = g->lm;
     line_of_graph(g, lvlab, lsrc, ldst, lelab, std::min<int64_t>(cap, g->lm));
     return GSI_OK;
-    EDGE_API_END
+    GSI_API_END
 }
 
 gsi_status gsi_edge_graph_device(const gsi_edge_graph *g, gsi_graph **line) {
@@ -288,7 +276,7 @@ gsi_status gsi_edge_query_line(const gsi_edge_graph *g, const int32_t *qvlab, in
                                const int32_t *qdst, const int32_t *qelab, int32_t qm, int32_t *lvlab,
                                int32_t *lsrc, int32_t *ldst, int32_t *lelab, int32_t cap, int32_t *lk,
                                int32_t *lqm) {
-    EDGE_API_BEGIN
+    GSI_API_BEGIN
     if (!g) {
         set_error("gsi_edge_query_line: null graph");
         return GSI_EINVAL;
@@ -303,13 +291,13 @@ gsi_status gsi_edge_query_line(const gsi_edge_graph *g, const int32_t *qvlab, in
     if (ldst) std::memcpy(ldst, d.data(), sizeof(int32_t) * c);
     if (lelab) std::memcpy(lelab, l.data(), sizeof(int32_t) * c);
     return GSI_OK;
-    EDGE_API_END
+    GSI_API_END
 }
 
 gsi_status gsi_edge_query_run(gsi_edge_graph *g, const int32_t *qvlab, int32_t k, const int32_t *qsrc,
                               const int32_t *qdst, const int32_t *qelab, int32_t qm, const gsi_query_opts *opts,
                               gsi_result **out) {
-    EDGE_API_BEGIN
+    GSI_API_BEGIN
     if (!g || !out) {
         set_error("gsi_edge_query_run: null graph or out");
         return GSI_EINVAL;
@@ -327,7 +315,7 @@ gsi_status gsi_edge_query_run(gsi_edge_graph *g, const int32_t *qvlab, int32_t k
     GSI_TRY(edge_query(g, qvlab, k, qsrc, qdst, qelab, qm, vl, s, d, l));
     return gsi_query_run(g->line, vl.data(), (int32_t)vl.size(), s.data(), d.data(), l.data(), (int32_t)s.size(),
                          opts, out);
-    EDGE_API_END
+    GSI_API_END
 }
 
 }  // extern "C"

@@ -41,6 +41,19 @@ struct gsi_result {
     ~gsi_result();
 };
 
+// Body of an extern "C" entry point: no exception crosses the ABI.
+#define GSI_API_BEGIN try {
+#define GSI_API_END                                                                            \
+    }                                                                                          \
+    catch (const std::bad_alloc &) {                                                           \
+        ::gsi::set_error("host allocation failed");                                            \
+        return GSI_ENOMEM;                                                                     \
+    }                                                                                          \
+    catch (...) {                                                                              \
+        ::gsi::set_error("unexpected host exception");                                         \
+        return GSI_ECUDA;                                                                      \
+    }
+
 namespace gsi {
 
 struct QueryGraph {
