@@ -7,7 +7,9 @@
  * mappings f: V(Q) -> V(G) that are injective, keep vertex labels and map
  * every query edge to a data edge with the same label.  It follows the
  * paper's two phases: signature filtering (Sec. III-A) and one vertex-oriented
- * join iteration per query vertex (Algs. 2-4, Sec. V).
+ * join iteration per query vertex (Algs. 2-4, Sec. V).  Sec. VII-A's
+ * homomorphism semantics is a query option; its edge isomorphism runs through
+ * the line-graph calls (gsi_edge_*).
  *
  * Conventions for every call:
  *   - Ids and labels are int32; counts are uint64.  Graphs are undirected and
