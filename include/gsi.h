@@ -15,8 +15,8 @@
  *   - Ids and labels are int32; counts are uint64.  Graphs are undirected and
  *     simple: one edge (and one label) per unordered vertex pair, no loops.
  *   - Input arrays are read during the call and copied; the caller keeps them.
- *   - Objects (gsi_graph, gsi_result, gsi_server) are owned by the library
- *     until the matching *_destroy call.
+ *   - Objects (gsi_graph, gsi_edge_graph, gsi_result, gsi_batch, gsi_server)
+ *     are owned by the library until the matching *_destroy call.
  *   - `stream` arguments are cudaStream_t values passed as void*; NULL means
  *     the legacy default stream.  Calls return after their results are
  *     ready unless stated otherwise.
