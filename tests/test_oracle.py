@@ -287,6 +287,35 @@ def test_join_step_rules():
     assert oracle.join_step(G, M, inC, [0, 1], [0, 0]).shape[0] == 0
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_join_step_output_within_the_alg4_bound(seed):
+    """Alg. 4's preallocation bound, stated in Sec. V: row i's output never
+    exceeds |N(v'_i, l0)| for whichever linking edge is taken as the first
+    edge.  So the preallocated area, the sum of those bounds (|GBA|, the last
+    offset of their exclusive scan), holds every survivor."""
+    rng = np.random.default_rng(3000 + seed)
+    for case in range(30):
+        n = int(rng.integers(8, 40))
+        g = H.random_graph(rng, n, float(rng.uniform(0.1, 0.5)), 2, 2)
+        if g.m == 0:
+            continue
+        G = og(g)
+        t = int(rng.integers(1, 4))
+        M = np.unique(np.array([rng.choice(n, t, replace=False) for _ in range(int(rng.integers(1, 30)))],
+                               np.int32), axis=0)                     # distinct rows, as in a table
+        d = int(rng.integers(1, t + 1))
+        cols = rng.choice(t, d, replace=False).tolist()
+        labs = rng.integers(0, 2, d).tolist()
+        in_c = rng.random(n) < 0.7
+        out = oracle.join_step(G, M, in_c, cols, labs)
+        nbrs = lambda v, l: sum(G.edge_label(int(v), w) == l for w in range(n))
+        for j in range(d):
+            caps = [nbrs(m[cols[j]], labs[j]) for m in M]
+            per_row = [int((out[:, :t] == m).all(axis=1).sum()) for m in M] if out.shape[0] else [0] * len(M)
+            assert all(c <= b for c, b in zip(per_row, caps)), (seed, case, j)
+            assert out.shape[0] <= sum(caps)
+
+
 def test_fingerprint_is_order_independent():
     rng = np.random.default_rng(1)
     rows = rng.integers(0, 1000, (500, 6)).astype(np.int32)
