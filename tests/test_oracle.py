@@ -325,6 +325,39 @@ def test_fingerprint_is_order_independent():
     assert fp[0] == 500
 
 
+def test_fingerprint_separates_sets_that_additive_mixes_confuse():
+    """The full-size parity tests compare fingerprints, so a wrong result must
+    change them even where column sums, per-column value multisets and the
+    row count stay the same: a column swap (a transposed operand), a +1/-1
+    shift of two ids (an off-by-one that cancels in any additive hash), and
+    two rows trading a value (right values, wrong rows)."""
+    rng = np.random.default_rng(7)
+    rows = np.unique(rng.integers(0, 5000, (2000, 5)).astype(np.int32), axis=0)
+    fp = oracle.fingerprint(rows)
+    for trial in range(20):
+        a, b = rng.choice(rows.shape[1], 2, replace=False)
+        swapped = rows.copy()
+        swapped[:, [a, b]] = swapped[:, [b, a]]
+        assert oracle.fingerprint(swapped) != fp
+        one = rows.copy()
+        r = rng.integers(rows.shape[0])
+        one[r, [a, b]] = one[r, [b, a]]
+        if not np.array_equal(one[r], rows[r]):
+            assert oracle.fingerprint(one) != fp
+        shifted = rows.copy()
+        r1, r2 = rng.choice(rows.shape[0], 2, replace=False)
+        c = rng.integers(rows.shape[1])
+        shifted[r1, c] += 1
+        shifted[r2, c] -= 1
+        assert shifted[:, c].sum() == rows[:, c].sum()
+        assert oracle.fingerprint(shifted) != fp
+        traded = rows.copy()
+        if traded[r1, c] != traded[r2, c]:
+            traded[r1, c], traded[r2, c] = rows[r2, c], rows[r1, c]
+            assert np.array_equal(np.sort(traded[:, c]), np.sort(rows[:, c]))
+            assert oracle.fingerprint(traded) != fp
+
+
 # ------------------------------------------------- homomorphism (Sec. VII-A)
 @pytest.mark.parametrize("block", range(4))
 def test_homomorphism_backtracking_equals_bruteforce(block):
