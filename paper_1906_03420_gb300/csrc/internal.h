@@ -93,6 +93,7 @@ struct JoinStep {
     int32_t lab[GSI_MAX_QUERY_VERTICES];
     int32_t perm[GSI_MAX_QUERY_VERTICES + 1];   // output position of each column
     int32_t hom = 0;                     // 1: homomorphism (no set subtraction, Sec. VII-A)
+    uint32_t inj = 0xffffffffu;          // columns whose query vertex has u's label (set subtraction)
 };
 
 constexpr int JOIN_NT = 256;
@@ -122,13 +123,14 @@ struct DStep {
     int32_t *out;                      // output table region
     uint64_t out_bytes;                // bytes of the output region
     uint64_t row_cap;                  // output rows allowed (0 = no limit)
-    uint64_t *S;                       // scratch region: F and part at the front, the per-row
-                                       // bound records (start, then length | edge) at the back
+    uint64_t *S;                       // scratch region: the long-row table (rows, bound
+                                       // records), its slot offsets F and tile partition
     uint64_t S_words;
     int32_t t, count_only;
     // set on the device
     unsigned long long count;          // survivors (exact even past out_cap); [0]: seed size
     unsigned long long next_tile;
+    unsigned long long nlong;          // rows set aside for the slot tiles (bound above SHORT_MAX)
     uint64_t R, total, ntiles, out_cap;
 };
 
@@ -153,9 +155,12 @@ gsi_status selftest_barrier_timeout(int dev, unsigned long long spin_limit, doub
 // the k step records (host-initialised static fields) and the zeroed control
 // words.  launch_query_coop then launches; bsum: QUERY_MAX_CTAS words.
 // steps[0].count receives |seed|.
+// memo: query_memo_tables(steps, k) tables of n 8-byte entries, zeroed before
+// the launch (per-vertex label sub-list locations, see join_rows.cuh), or null.
+int query_memo_tables(const std::vector<JoinStep> &steps, int k);
 gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
-                              const int32_t *order, int count_only, unsigned long long *stats, void *cfg_host,
-                              size_t *smem);
+                              const int32_t *order, int count_only, unsigned long long *stats, uint64_t *memo,
+                              void *cfg_host, size_t *smem);
 gsi_status launch_query_coop(const gsi_graph *g, int k, const uint32_t *seed_bitmap, size_t smem, void *cfg_dev,
                              DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out,
                              cudaStream_t stream);

@@ -50,6 +50,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "join_rows.cuh"
 #include "join_tile.cuh"
 #include "scan.cuh"
 
@@ -168,15 +169,87 @@ __device__ __forceinline__ void cta_prefix(const unsigned long long *bsum, unsig
     *tot = block_sum<JOIN_NT, unsigned long long>(q, wt);
 }
 
+// The long rows of a step (bound above SHORT_MAX) through the candidate-slot
+// tiles: per-CTA slot sums, slot offsets F, the first row of every tile, then
+// the tiles from a counter, with a grid barrier after each phase.  Survivors
+// join those of the row pass in st->out.  False when a barrier wait gave up
+// or the partition does not fit (fail bit 1).
 template <int NT, int VT>
-__global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs, DStep *steps, int k, QueryCtl *ctl,
-                                              const uint32_t *__restrict__ seed_bitmap, int64_t nwords,
-                                              unsigned long long *bsum) {
+__device__ __forceinline__ bool long_rows_join(const JoinArgs &a, DStep *st, QueryCtl *ctl, const LongTable &lt,
+                                               uint64_t L, uint64_t *F, int64_t *part, uint64_t part_cap,
+                                               uint64_t cap, unsigned long long *bsum, unsigned long long *wt,
+                                               unsigned long long *tile_s) {
     constexpr int NV = NT * VT;
-    __shared__ unsigned long long wt[NT / 32];
-    __shared__ unsigned long long tile_s;
     const unsigned G = gridDim.x;
     const uint64_t W = (uint64_t)JOIN_ROW_WEIGHT;
+    unsigned long long pre, tot;
+    // slots of each long row: its bound plus W staging slots; per-CTA sums
+    const uint64_t per = (L + G - 1) / G;
+    const uint64_t chunk = (per + SCAN_NV - 1) / SCAN_NV * SCAN_NV;
+    const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(L, lo + chunk);
+    unsigned long long sum = 0;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += NT) sum += (unsigned long long)(__ldcg(lt.bnd + i) & BOUND_LEN_MASK) + W;
+    sum = block_sum<NT, unsigned long long>(sum, wt);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = sum;
+    if (!grid_barrier(ctl, G)) return false;
+    // slot offsets F over the long rows
+    cta_prefix(bsum, G, wt, &pre, &tot);
+    const uint64_t total = tot;
+    const uint64_t ntiles = (total + NV - 1) / NV;
+    if (ntiles + 1 > part_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
+        return false;
+    }
+    {
+        unsigned long long run = pre;
+        for (uint64_t base = lo; base < hi; base += NT) {
+            const uint64_t i = base + threadIdx.x;
+            const unsigned long long v = i < hi ? (unsigned long long)(__ldcg(lt.bnd + i) & BOUND_LEN_MASK) + W : 0ull;
+            unsigned long long t2;
+            const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(v, wt, &t2) + run;
+            if (i < hi) F[i] = ex;
+            run += t2;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        F[L] = total;
+        st->total = total;
+        st->ntiles = ntiles;
+    }
+    if (!grid_barrier(ctl, G)) return false;
+    // first long row of every tile
+    for (uint64_t b = (uint64_t)blockIdx.x * NT + threadIdx.x; b <= ntiles; b += (uint64_t)G * NT) {
+        const uint64_t sl = min(b * (uint64_t)NV, total);
+        int64_t l2 = 0, h2 = (int64_t)L;
+        while (l2 < h2) {
+            int64_t mid = (l2 + h2 + 1) >> 1;
+            if (__ldcg(F + mid) <= sl) l2 = mid;
+            else h2 = mid - 1;
+        }
+        part[b] = l2;
+    }
+    if (!grid_barrier(ctl, G)) return false;
+    // the join tiles, taken from a counter
+    for (;;) {
+        if (threadIdx.x == 0) *tile_s = atomicAdd(&st->next_tile, 1ull);
+        __syncthreads();
+        const uint64_t tile = *tile_s;
+        if (tile >= ntiles) break;
+        join_tile<NT, VT, false, true>(a, lt.rows, (int64_t)L, F, total, __ldcg(part + tile), __ldcg(part + tile + 1),
+                                       st->out, cap, &st->count, tile, lt.bnd, lt.blo);
+    }
+    return grid_barrier(ctl, G);
+}
+
+template <int NT, int VT>
+__global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cfgs, DStep *steps, int k, QueryCtl *ctl,
+                                              const uint32_t *__restrict__ seed_bitmap, int64_t nwords,
+                                              unsigned long long *bsum) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long wt[NT / 32];
+    __shared__ unsigned long long tile_s;
+    __shared__ __align__(16) JoinArgs a_s;
+    const unsigned G = gridDim.x;
     unsigned long long pre, tot;
 
     // ---- seed: C(u_first) as the one-column table in the first region (Alg. 2)
@@ -210,102 +283,50 @@ __global__ void __launch_bounds__(NT) k_query(const JoinArgs *__restrict__ cfgs,
 
     for (int t = 1; t < k; ++t) {
         DStep *st = steps + t;
-        const JoinArgs &a = cfgs[t];
+        {   // this step's configuration, once per CTA, in shared memory
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(cfgs + t);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&a_s);
+            for (int i = threadIdx.x; i < (int)(sizeof(JoinArgs) / 4); i += NT) dst[i] = src[i];
+        }
+        const JoinArgs &a = a_s;
         const uint64_t R = __ldcg(&steps[t - 1].count);
-        // the previous table must have fit its region; the scratch must fit too
+        // the previous table must have fit its region
         if (t > 1 && R > __ldcg(&steps[t - 1].out_cap)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 2u);
             return;
         }
-        if ((R + 1) * 8 + R * 8 + 64 > st->S_words * 8) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
-            return;
-        }
-        uint64_t *F = st->S;
-        // per-row bound records at the end of the scratch region: length and
-        // linking-edge index of the shortest sub-list, and its start
-        uint32_t *caps = reinterpret_cast<uint32_t *>(st->S + st->S_words) - R;
-        uint32_t *blo = caps - R;
-        const int32_t *M = st->M;
-        // phase 1: each row's bound (the shortest label sub-list), per-CTA sums
-        const uint64_t per = (R + G - 1) / G;
-        const uint64_t chunk = (per + SCAN_NV - 1) / SCAN_NV * SCAN_NV;
-        const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(R, lo + chunk);
-        unsigned long long sum = 0, abytes = 0;
-        bool too_long = false;
-        for (uint64_t i = lo + threadIdx.x; i < hi; i += NT) {
-            uint32_t lob;
-            int jb;
-            uint64_t lsum;
-            const uint32_t c = row_bound_full(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lob, &jb, &lsum);
-            if (a.stats) abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
-            too_long |= c > BOUND_LEN_MASK;
-            caps[i] = (c & BOUND_LEN_MASK) | ((uint32_t)jb << BOUND_LEN_BITS);
-            blo[i] = lob;
-            sum += (unsigned long long)c + W;
-        }
-        if (too_long) atomicOr(&ctl->fail, 1u);    // a sub-list too long for the record: splitting path
-        sum = block_sum<NT, unsigned long long>(sum, wt);
-        if (threadIdx.x == 0) bsum[blockIdx.x] = sum;
-        if (a.stats) {                       // one add per CTA and step
-            abytes = block_sum<NT, unsigned long long>(abytes, wt);
-            if (threadIdx.x == 0 && abytes) atomicAdd(a.stats, abytes);
-        }
-        if (!grid_barrier(ctl, G)) return;
-        // phase 2: slot offsets F (each CTA rescans its own chunk)
-        cta_prefix(bsum, G, wt, &pre, &tot);
-        const uint64_t total = tot;
-        const uint64_t ntiles = (total + NV - 1) / NV;
-        int64_t *part = reinterpret_cast<int64_t *>(st->S + R + 1);
+        const LongLayout ll = long_layout(st->S_words, t);
+        LongTable lt;
+        lt.rows = reinterpret_cast<int32_t *>(st->S);
+        lt.bnd = reinterpret_cast<uint32_t *>(lt.rows + ll.cap * (uint64_t)t);
+        lt.blo = lt.bnd + ll.cap;
+        lt.cap = ll.cap;
+        lt.count = &st->nlong;
         uint64_t cap = st->out_bytes / (4ull * (uint64_t)(t + 1));
         if (st->row_cap && st->row_cap < cap) cap = st->row_cap;
         if (st->count_only) cap = 0;
-        if ((R + 1 + ntiles + 1) * 8 + R * 8 + 64 > st->S_words * 8) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->fail, 1u);
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->out_cap = cap;
+        __syncthreads();
+        // ---- short rows joined inline, long rows set aside (one pass over M)
+        unsigned long long abytes = 0, items = 0;
+        row_pass<NT>(a, st->M, R, (uint64_t)blockIdx.x * NT, (uint64_t)G * NT, st->out, cap, &st->count, lt, &ctl->fail,
+                     smem, &abytes, &items);
+        if (a.stats) {                       // one add per CTA and step
+            abytes = block_sum<NT, unsigned long long>(abytes, wt);
+            items = block_sum<NT, unsigned long long>(items, wt);
+            if (threadIdx.x == 0) {
+                if (abytes) atomicAdd(a.stats, abytes);
+                if (items) atomicAdd(a.stats + 1, items);
+            }
+        }
+        if (!grid_barrier(ctl, G)) return;
+        if (__ldcg(&ctl->fail) & 1u) return;                  // long-row table full: a larger arena
+        // ---- long rows through the candidate-slot tiles
+        const uint64_t L = __ldcg(lt.count);
+        if (L > 0 && !long_rows_join<NT, VT>(a, st, ctl, lt, L, st->S + ll.f_off,
+                                             reinterpret_cast<int64_t *>(st->S + ll.part_off), ll.part_cap, cap,
+                                             bsum, wt, &tile_s))
             return;
-        }
-        {
-            unsigned long long run = pre;
-            for (uint64_t base = lo; base < hi; base += NT) {
-                const uint64_t i = base + threadIdx.x;
-                const unsigned long long v = i < hi ? (unsigned long long)(caps[i] & BOUND_LEN_MASK) + W : 0ull;
-                unsigned long long t2;
-                const unsigned long long ex = block_exclusive_scan<NT, unsigned long long>(v, wt, &t2) + run;
-                if (i < hi) F[i] = ex;
-                run += t2;
-            }
-        }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            F[R] = total;
-            st->R = R;
-            st->total = total;
-            st->ntiles = ntiles;
-            st->out_cap = cap;
-            if (a.stats) atomicAdd(a.stats + 1, (unsigned long long)(total - W * R));   // candidate slots
-        }
-        if (!grid_barrier(ctl, G)) return;
-        // phase 3: first row of every tile
-        for (uint64_t b = (uint64_t)blockIdx.x * NT + threadIdx.x; b <= ntiles; b += (uint64_t)G * NT) {
-            const uint64_t sl = min(b * (uint64_t)NV, total);
-            int64_t l2 = 0, h2 = (int64_t)R;
-            while (l2 < h2) {
-                int64_t mid = (l2 + h2 + 1) >> 1;
-                if (__ldcg(F + mid) <= sl) l2 = mid;
-                else h2 = mid - 1;
-            }
-            part[b] = l2;
-        }
-        if (!grid_barrier(ctl, G)) return;
-        // phase 4: the join tiles, taken from a counter
-        for (;;) {
-            if (threadIdx.x == 0) tile_s = atomicAdd(&st->next_tile, 1ull);
-            __syncthreads();
-            const uint64_t tile = tile_s;
-            if (tile >= ntiles) break;
-            join_tile<NT, VT, false, true>(a, M, (int64_t)R, F, total, __ldcg(part + tile), __ldcg(part + tile + 1),
-                                           st->out, cap, &st->count, tile, caps, blo);
-        }
-        if (!grid_barrier(ctl, G)) return;
         if (a.stats && blockIdx.x == 0 && threadIdx.x == 0)        // survivors written
             atomicAdd(a.stats, 4ull * (uint64_t)(t + 1) * min((uint64_t)__ldcg(&st->count), cap));
     }
@@ -325,6 +346,8 @@ StepDev step_dev(const gsi_graph *g, const JoinStep &s) {
     d.L = g->L;
     d.ulab = s.ulab;
     d.hom = s.hom;
+    const uint32_t tmask = s.t >= 32 ? 0xffffffffu : ((1u << s.t) - 1u);
+    d.inj = s.hom ? 0u : (s.inj & tmask);
     for (int i = 0; i < GSI_MAX_QUERY_VERTICES; ++i) {
         d.col[i] = i < s.d ? s.col[i] : 0;
         d.lab[i] = i < s.d ? s.lab[i] : 0;
@@ -418,16 +441,25 @@ JoinArgs make_join_args(const gsi_graph *g, const JoinStep &s, const uint32_t *c
 
 size_t join_args_size() { return sizeof(JoinArgs); }
 
+int query_memo_tables(const std::vector<JoinStep> &steps, int k) {
+    int m = 0;
+    for (int t = 1; t < k; ++t) m = std::max(m, std::min(steps[t].d, MEMO_EDGES));
+    return m;
+}
+
 gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
-                              const int32_t *order, int count_only, unsigned long long *stats, void *cfg_host,
-                              size_t *smem) {
+                              const int32_t *order, int count_only, unsigned long long *stats, uint64_t *memo,
+                              void *cfg_host, size_t *smem) {
     JoinArgs *cfg = static_cast<JoinArgs *>(cfg_host);
     std::memset(cfg, 0, sizeof(JoinArgs));
     size_t sm = 0;
     for (int t = 1; t < k; ++t) {
         const int co = (t == k - 1) && count_only;
         cfg[t] = make_join_args(g, steps[t], bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords, co, stats);
+        cfg[t].memo = memo;
+        cfg[t].memo_n = g->n;
         sm = std::max(sm, join_smem(cfg[t].rmax, steps[t].t, steps[t].d));
+        sm = std::max(sm, rows_smem(JOIN_NT, steps[t].t, SHORT_MAX));
     }
     if (sm > 200 * 1024) {
         set_error("join: shared memory need exceeds 200 KB");

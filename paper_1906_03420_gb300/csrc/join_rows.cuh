@@ -1,0 +1,295 @@
+// The row pass of a join step: short rows joined by one thread each, long
+// rows set aside for the candidate-slot tiles.
+//
+// Most rows of the large steps have one or two candidates in their shortest
+// label sub-list (the Alg. 4 bound).  For such a row the slot-tile path pays
+// more for the bookkeeping (a bound record, a slot offset, a tile partition,
+// staging, a slot-to-row map and W staging slots) than for the join itself.
+// Here one thread takes one row from its bound to its survivors in a single
+// pass:
+//   * a CTA stages NT consecutive rows of M with coalesced loads;
+//   * each thread finds its row's shortest label sub-list over the linking
+//     edges (the output bound, Alg. 4);
+//   * when that bound is at most SHORT_MAX, the thread tests every candidate
+//     (bitmap of C(u), set subtraction against the row, membership in the
+//     other linking lists: Alg. 3's set operations) and keeps a bit mask of
+//     survivors;
+//   * otherwise the row, with its bound record (length, linking edge, start),
+//     is appended to a long-row table that the slot tiles process after a
+//     grid barrier (a hub row then spreads over many CTAs, Sec. VI-A's load
+//     balancing done by the tiles);
+//   * one block-wide scan and one atomic per CTA and batch place the batch's
+//     survivors in M', which the CTA writes as one coalesced run
+//     (Prealloc-Combine without a second join: each survivor is written
+//     once).
+//
+// Shared work between rows (duplicate removal, Sec. VI-B).  Rows of a step
+// reuse few data vertices: consecutive rows of M' often extend the same
+// row of M, and hubs recur everywhere.  Two mechanisms keep rows from
+// repeating each other's work:
+//   * a per-step memo holds, for each data vertex v and each of the first
+//     MEMO_EDGES linking edges, where the label(u) sub-list of N(v, l) starts
+//     and how long it is; a row whose vertex is in the memo skips the list
+//     lookup and the label-range search (entries carry the step number, so a
+//     stale entry is a miss, never a wrong answer);
+//   * in single-edge steps the lanes of a warp whose rows share the first-edge
+//     vertex v (found with __match_any_sync) elect one lane, which locates the
+//     sub-list and probes the candidate bitmap C(u) for the whole group once;
+//     the other lanes receive the bound and the bitmap mask by shuffle and
+//     only add their own set subtraction, as Alg. 5 shares one N(v, l0)
+//     fetch among the rows of a block that have the same m_i[u0'].
+#pragma once
+
+#include "join_tile.cuh"
+
+namespace gsi {
+
+constexpr int SHORT_MAX = 16;     // rows with at most this many candidates are joined inline
+constexpr int MEMO_EDGES = 4;     // linking edges of a step with a sub-list memo
+constexpr uint32_t MEMO_TAG_SHIFT = 59;
+
+// Rows whose bound exceeds SHORT_MAX, copied (t columns) with their bound
+// records, for the slot tiles.  count is a device counter.
+struct LongTable {
+    int32_t *rows;
+    uint32_t *bnd;                // length | linking edge << BOUND_LEN_BITS
+    uint32_t *blo;                // start of the shortest sub-list
+    uint64_t cap;                 // rows the table holds
+    unsigned long long *count;
+};
+
+// Layout of the long-row table of step t in a scratch region of S_words
+// 8-byte words: rows, bound records, then F; the tile partition takes what is
+// left (at least an eighth of the region).
+struct LongLayout {
+    uint64_t cap, f_off, part_off, part_cap;    // offsets in words
+};
+__host__ __device__ inline LongLayout long_layout(uint64_t S_words, int t) {
+    LongLayout l;
+    const uint64_t avail = S_words > 64 ? S_words - S_words / 8 - 8 : 0;
+    l.cap = avail * 8 / (4ull * (uint64_t)t + 16ull);
+    const uint64_t rec_words = (l.cap * (4ull * (uint64_t)t + 8ull) + 7) / 8;
+    l.f_off = rec_words;
+    l.part_off = l.f_off + l.cap + 1;
+    l.part_cap = S_words > l.part_off ? S_words - l.part_off : 0;
+    return l;
+}
+
+// Dynamic shared memory of the row pass: NT staged rows of t columns, then
+// the batch's survivors (value, local row).
+__host__ __device__ constexpr size_t rows_smem(int nt, int t, int s) {
+    return (size_t)nt * (size_t)t * 4 + (size_t)nt * (size_t)s * 4 + (size_t)nt * (size_t)s;
+}
+
+// Start (*lo) and length (returned) of the label(u) sub-list of N(v, lab[j]),
+// through the memo when the step has one.  A memo entry is
+// start | length << 32 | step << MEMO_TAG_SHIFT; concurrent writers store the
+// same value, and a load that sees an older entry (another step's, or a
+// stale cached line) only recomputes it.
+__device__ __forceinline__ uint32_t sublist(const JoinArgs &a, int j, int32_t v, uint32_t *lo) {
+    uint64_t *slot = nullptr;
+    if (a.memo && j < MEMO_EDGES) {
+        slot = a.memo + (uint64_t)j * (uint64_t)a.memo_n + (uint32_t)v;
+        const uint64_t e = *slot;
+        if ((uint32_t)(e >> MEMO_TAG_SHIFT) == (uint32_t)a.s.t) {
+            *lo = (uint32_t)e;
+            return (uint32_t)(e >> 32) & BOUND_LEN_MASK;
+        }
+    }
+    const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+    const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
+    uint32_t l, h;
+    label_range(a.cl, x0, x1, (uint32_t)a.s.ulab, &l, &h);
+    *lo = l;
+    const uint32_t len = h - l;
+    if (slot && len <= BOUND_LEN_MASK)
+        *slot = (uint64_t)l | ((uint64_t)len << 32) | ((uint64_t)(uint32_t)a.s.t << MEMO_TAG_SHIFT);
+    return len;
+}
+
+// Candidates ci[lo + p], p < len <= 32, that are in C(u): bit p of the result.
+__device__ __forceinline__ uint32_t bitmap_mask(const JoinArgs &a, uint32_t lo, uint32_t len) {
+    uint32_t mask = 0;
+    for (uint32_t p0 = 0; p0 < len; p0 += 4) {
+        int32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = p0 + q < len ? __ldg(a.ci + lo + p0 + q) : -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (w[q] >= 0 && ((__ldg(a.cand + (w[q] >> 5)) >> (w[q] & 31)) & 1u)) mask |= 1u << (p0 + q);
+    }
+    return mask;
+}
+
+// Clears the bits of `mask` whose candidate equals a value of the row in a
+// column the set subtraction tests (only columns whose query vertex carries
+// u's label can hold w; none under homomorphism).
+__device__ __forceinline__ uint32_t subtract_row(const JoinArgs &a, const int32_t *row, uint32_t lo, uint32_t mask) {
+    const uint32_t inj = a.s.inj;
+    if (!inj) return mask;
+    for (uint32_t m = mask; m; m &= m - 1) {
+        const int p = __ffs(m) - 1;
+        const int32_t w = __ldg(a.ci + lo + (uint32_t)p);
+        for (uint32_t im = inj; im; im &= im - 1)
+            if (row[__ffs(im) - 1] == w) {
+                mask &= ~(1u << p);
+                break;
+            }
+    }
+    return mask;
+}
+
+// The row pass over rows [first, R) in batches of NT rows, batch starts
+// `stride` apart (a grid-strided pass: first = blockIdx.x * NT, stride =
+// gridDim.x * NT; one CTA alone: first = 0, stride = NT).  `a` should live in
+// shared memory.  Survivors go to out (up to cap rows; `count` is exact),
+// long rows to lt.  Bit 1 of *fail is set when the long-row table is full or
+// a bound does not fit its record.  Adds this thread's algorithmic bytes
+// (rows read, lists located and read; survivors are counted by the caller)
+// and candidate slots to *abytes / *items when a.stats is set.
+template <int NT, bool DR = true>
+__device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64_t first, uint64_t stride,
+                         int32_t *__restrict__ out, uint64_t cap, unsigned long long *count, const LongTable &lt,
+                         unsigned *fail, unsigned char *smem, unsigned long long *abytes,
+                         unsigned long long *items) {
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t wt[NW];
+    __shared__ unsigned long long base_s, lbase_s;
+    const int t = a.s.t, d = a.s.d, W1 = t + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *rowv = reinterpret_cast<int32_t *>(smem);                  // NT * t
+    int32_t *comp_w = rowv + NT * t;                                    // NT * SHORT_MAX
+    uint8_t *comp_r = reinterpret_cast<uint8_t *>(comp_w + NT * SHORT_MAX);
+    const bool stats = a.stats != nullptr;
+    const bool write = cap > 0;
+    // the output loop's fixed lane map: lane = rs * W1 + c writes column c of
+    // the rs-th of the warp's rpw rows per round
+    const int rpw = 32 / W1, rs = lane / W1, oc = lane - rs * W1;
+    const int src_col = a.iperm[oc < W1 ? oc : 0];
+    for (uint64_t r0 = first; r0 < R; r0 += stride) {
+        const int nb = (int)min((uint64_t)NT, R - r0);
+        const int32_t *src = M + r0 * (uint64_t)t;
+        for (int e = threadIdx.x; e < nb * t; e += NT) rowv[e] = __ldcg(src + e);
+        __syncthreads();
+        const bool valid = threadIdx.x < nb;
+        const int32_t *row = rowv + (valid ? threadIdx.x : 0) * t;
+        uint32_t mask = 0, best = 0, lob = 0;
+        int jb = 0;
+        if (DR && d == 1) {
+            // rows of the warp that share the first-edge vertex share its
+            // sub-list and bitmap probes: one lane works for the group
+            const int32_t v = valid ? row[a.s.col[0]] : -1 - lane;
+            const unsigned peers = __match_any_sync(FULL_MASK, v);
+            const int leader = __ffs(peers) - 1;
+            uint32_t bm = 0;
+            if (lane == leader && valid) {
+                best = sublist(a, 0, v, &lob);
+                if (best <= (uint32_t)SHORT_MAX) bm = bitmap_mask(a, lob, best);
+            }
+            best = __shfl_sync(FULL_MASK, best, leader);
+            lob = __shfl_sync(FULL_MASK, lob, leader);
+            bm = __shfl_sync(FULL_MASK, bm, leader);
+            if (valid && best <= (uint32_t)SHORT_MAX) mask = subtract_row(a, row, lob, bm);
+            if (valid && stats) {
+                *abytes += row_alg_bytes(t, 1, best, best);
+                *items += best;
+            }
+        } else if (valid) {
+            // the shortest label sub-list over the linking edges
+            uint32_t lo4[MEMO_EDGES], len4[MEMO_EDGES];
+            uint64_t lsum = 0;
+            best = 0xffffffffu;
+#pragma unroll
+            for (int j = 0; j < MEMO_EDGES; ++j) {
+                lo4[j] = 0;
+                len4[j] = 0;
+                if (j < d) {
+                    len4[j] = sublist(a, j, row[a.s.col[j]], &lo4[j]);
+                    lsum += len4[j];
+                    if (len4[j] < best) {
+                        best = len4[j];
+                        lob = lo4[j];
+                        jb = j;
+                    }
+                }
+            }
+            for (int j = MEMO_EDGES; j < d; ++j) {
+                uint32_t l;
+                const uint32_t n = sublist(a, j, row[a.s.col[j]], &l);
+                lsum += n;
+                if (n < best) {
+                    best = n;
+                    lob = l;
+                    jb = j;
+                }
+            }
+            if (stats) {
+                *abytes += row_alg_bytes(t, d, lsum, best);
+                *items += best;
+            }
+            if (best > 0 && best <= (uint32_t)SHORT_MAX) {
+                mask = subtract_row(a, row, lob, bitmap_mask(a, lob, best));
+                // every other linking list must hold the candidate (Alg. 3)
+                for (uint32_t m = mask; m; m &= m - 1) {
+                    const int p = __ffs(m) - 1;
+                    const int32_t w = __ldg(a.ci + lob + (uint32_t)p);
+                    bool ok = true;
+#pragma unroll
+                    for (int j = 0; j < MEMO_EDGES; ++j)
+                        if (ok && j < d && j != jb) ok = sorted_contains(a.ci + lo4[j], len4[j], w);
+                    for (int j = MEMO_EDGES; j < d && ok; ++j) {
+                        if (j == jb) continue;
+                        const uint64_t seg =
+                            (uint64_t)(uint32_t)row[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+                        ok = ranked_contains(a.ci, a.cl, __ldg(a.off + seg), __ldg(a.off + seg + 1),
+                                             (uint32_t)a.s.ulab, w);
+                    }
+                    if (!ok) mask &= ~(1u << p);
+                }
+            }
+        }
+        const bool lng = valid && best > (uint32_t)SHORT_MAX;
+        const uint32_t n = __popc(mask);
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<NT, uint32_t>(n | ((uint32_t)lng << 16), wt, &tot);
+        const uint32_t ntot = tot & 0xffffu, ltot = tot >> 16;
+        if (threadIdx.x == 0) {
+            base_s = ntot ? atomicAdd(count, (unsigned long long)ntot) : 0ull;
+            lbase_s = ltot ? atomicAdd(lt.count, (unsigned long long)ltot) : 0ull;
+        }
+        if (write && mask) {                 // survivors to their place in the batch's run
+            uint32_t i = ex & 0xffffu;
+            for (uint32_t m = mask; m; m &= m - 1) {
+                comp_w[i] = __ldg(a.ci + lob + (uint32_t)(__ffs(m) - 1));
+                comp_r[i] = (uint8_t)threadIdx.x;
+                ++i;
+            }
+        }
+        __syncthreads();
+        if (lng) {
+            const unsigned long long li = lbase_s + (ex >> 16);
+            if (li < lt.cap && best <= BOUND_LEN_MASK) {
+                int32_t *dst = lt.rows + li * (uint64_t)t;
+                for (int c = 0; c < t; ++c) dst[c] = row[c];
+                lt.bnd[li] = best | ((uint32_t)jb << BOUND_LEN_BITS);
+                lt.blo[li] = lob;
+            } else {
+                atomicOr(fail, 1u);
+            }
+        }
+        if (write && ntot) {
+            const uint64_t base = base_s;
+            const uint64_t room = cap > base ? cap - base : 0;
+            const uint32_t nrow = (uint32_t)min((uint64_t)ntot, room);
+            int32_t *dst = out + base * (uint64_t)W1;
+            if (rs < rpw)
+                for (uint32_t r = (uint32_t)(warp * rpw + rs); r < nrow; r += (uint32_t)(NW * rpw)) {
+                    const int32_t val = src_col == t ? comp_w[r] : rowv[(int)comp_r[r] * t + src_col];
+                    dst[(uint64_t)r * W1 + oc] = val;
+                }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace gsi

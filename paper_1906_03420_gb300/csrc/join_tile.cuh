@@ -30,6 +30,8 @@ __device__ inline void label_range(const uint16_t *__restrict__ cl, uint32_t a, 
 struct StepDev {
     int32_t t, d, L, ulab;
     int32_t hom;                // 1: no set subtraction (homomorphism, Sec. VII-A)
+    uint32_t inj;               // columns the set subtraction tests: those whose query vertex
+                                // carries u's label (no other column can hold w); 0 under hom
     int32_t col[GSI_MAX_QUERY_VERTICES];
     int32_t lab[GSI_MAX_QUERY_VERTICES];
 };
@@ -123,6 +125,10 @@ struct JoinArgs {
     int32_t W, rmax, count_only;
     StepDev s;
     int32_t iperm[GSI_MAX_QUERY_VERTICES + 1];   // output column oc holds input position iperm[oc]
+    // per-vertex memo of label sub-list locations for the first linking edges
+    // (null: none); table j holds n entries, tagged with the step
+    uint64_t *memo;
+    int64_t memo_n;
 };
 
 template <int NT>
@@ -288,8 +294,7 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         const int32_t w = __ldg(a.ci + (uint64_t)base0[lr] + (uint64_t)p);
         bool ok = (__ldg(a.cand + (w >> 5)) >> (w & 31)) & 1u;
         const int32_t *rv = rowv + lr * t;
-        if (!a.s.hom)
-            for (int c = 0; c < t && ok; ++c) ok = rv[c] != w;
+        for (uint32_t im = a.s.inj; ok && im; im &= im - 1) ok = rv[__ffs(im) - 1] != w;
         for (int j = 0; j < dm1 && ok; ++j) {
             const uint32_t *ls = lst + (lr * dm1 + j) * 2;
             if (PRE) ok = ranked_contains(a.ci, a.cl, ls[0], ls[0] + ls[1], (uint32_t)a.s.ulab, w);

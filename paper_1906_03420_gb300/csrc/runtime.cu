@@ -182,6 +182,11 @@ void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first,
             ++s.d;
         }
         for (int c = 0; c <= p; ++c) s.perm[c] = (p == k - 1) ? order[c] : c;
+        // only a column whose query vertex carries u's label can hold u's
+        // image, so the set subtraction tests those columns alone
+        s.inj = 0;
+        for (int c = 0; c < p; ++c)
+            if (ranks[order[c]] == ranks[u]) s.inj |= 1u << c;
     }
 }
 
@@ -389,16 +394,19 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
         *no_memory = true;
         return GSI_OK;
     }
-    uint64_t *S = nullptr;
+    uint64_t *S = nullptr, *memo = nullptr;
     int32_t *reg[2] = {nullptr, nullptr};
     unsigned char *ctl = nullptr;
+    const uint64_t memo_bytes = (uint64_t)query_memo_tables(steps, k) * (uint64_t)g->n * 8;
     const size_t ctl_bytes = (join_args_size() * (size_t)k + 255) / 256 * 256 +
                              (sizeof(DStep) * (size_t)k + 255) / 256 * 256 + 256 + 8 * (size_t)QUERY_MAX_CTAS;
     gsi_status rc = dalloc(*this, (void **)&S, s_bytes);
     if (rc == GSI_OK) rc = dalloc(*this, (void **)&reg[0], t_bytes);
     if (rc == GSI_OK) rc = dalloc(*this, (void **)&reg[1], t_bytes);
     if (rc == GSI_OK) rc = dalloc(*this, (void **)&ctl, ctl_bytes);
+    if (rc == GSI_OK && memo_bytes) rc = dalloc(*this, (void **)&memo, memo_bytes);
     auto release = [&]() {
+        if (memo) cudaFreeAsync(memo, st);
         if (S) cudaFreeAsync(S, st);
         if (reg[0]) cudaFreeAsync(reg[0], st);
         if (reg[1]) cudaFreeAsync(reg[1], st);
@@ -431,7 +439,7 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     }
     unsigned long long *jstats = stats ? d_scalars + 1 : nullptr;
     size_t smem = 0;
-    rc = query_coop_configs(g, steps, k, bitmaps, order, count_only, jstats, h_stage, &smem);
+    rc = query_coop_configs(g, steps, k, bitmaps, order, count_only, jstats, memo, h_stage, &smem);
     if (rc != GSI_OK) {
         release();
         return rc;
@@ -452,7 +460,11 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
         h.t = t;
     }
     rc = GSI_OK;
-    if (cudaMemcpyAsync(ctl, h_stage, up_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    if (memo_bytes && cudaMemsetAsync(memo, 0, memo_bytes, st) != cudaSuccess) {
+        set_error("device-driven join: clearing the sub-list memo failed");
+        rc = GSI_ECUDA;
+    }
+    if (rc == GSI_OK && cudaMemcpyAsync(ctl, h_stage, up_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         set_error("device-driven join: control upload failed");
         rc = GSI_ECUDA;
     }
