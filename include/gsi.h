@@ -237,10 +237,12 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
  * process exits.  Limits: R <= 2^20 rows and at most 2^28 candidate slots (sum
  * over rows of the row's output bound + 2); larger calls return GSI_EINVAL with
  * a message.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the array and it keeps the previous call's contents (the
- * survivor counter is cleared per call); calls that overlap on the GPU race
- * on it and must be serialised by the caller.  Calls no allocator.
+ * (cudaGetSymbolAddress) and keeps it.  Every call synchronises `stream` and
+ * reads sizes back to pageable host memory, so no call may be made while
+ * that stream is being captured into a CUDA graph.  Every call shares the
+ * array and it keeps the previous call's contents (the survivor counter is
+ * cleared per call); calls that overlap on the GPU race on it and must be
+ * serialised by the caller.  Calls no allocator.
  */
 gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, const uint32_t *cand,
                                  int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d, int32_t *out,

@@ -42,6 +42,38 @@ gsi::ResultArena::~ResultArena() {
     if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }
 
+namespace gsi {
+gsi_status join_step_args(const char *who, gsi_graph *g, const int32_t *M, uint64_t R, int32_t t,
+                          const uint32_t *cand, int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d,
+                          int32_t *out, uint64_t out_cap, uint64_t *count, JoinStep *s, bool *empty) {
+    if (!g || !count || !col || !lab || (R > 0 && (!M || !cand)) || (out_cap > 0 && !out)) {
+        set_error(std::string(who) + ": null argument");
+        return GSI_EINVAL;
+    }
+    if (t < 1 || t >= GSI_MAX_QUERY_VERTICES || d < 1 || d > t) {
+        set_error(std::string(who) + ": need 1 <= d <= t < 32");
+        return GSI_EINVAL;
+    }
+    s->t = t;
+    s->d = d;
+    s->ulab = g->label_rank(ulabel);
+    bool none = s->ulab < 0;
+    for (int j = 0; j < d; ++j) {
+        if (col[j] < 0 || col[j] >= t || lab[j] < 0) {
+            set_error(std::string(who) + ": column out of range or negative label");
+            return GSI_EINVAL;
+        }
+        s->col[j] = col[j];
+        s->lab[j] = lab[j];
+        none |= lab[j] >= g->L;
+    }
+    for (int c = 0; c <= t; ++c) s->perm[c] = c;
+    *count = 0;
+    *empty = R == 0 || none;
+    return GSI_OK;
+}
+}  // namespace gsi
+
 extern "C" {
 
 const char *gsi_version(void) { return "gsi-gb300 0.1 (sm_103a)"; }
@@ -260,31 +292,10 @@ gsi_status gsi_join_step(gsi_graph *g, const int32_t *M, uint64_t R, int32_t t, 
                          int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d, int32_t *out,
                          uint64_t out_cap, uint64_t *count, void *stream) {
     GSI_API_BEGIN
-    if (!g || !count || !col || !lab || (R > 0 && (!M || !cand)) || (out_cap > 0 && !out)) {
-        set_error("gsi_join_step: null argument");
-        return GSI_EINVAL;
-    }
-    if (t < 1 || t >= GSI_MAX_QUERY_VERTICES || d < 1 || d > t) {
-        set_error("gsi_join_step: need 1 <= d <= t < 32");
-        return GSI_EINVAL;
-    }
     JoinStep s;
-    s.t = t;
-    s.d = d;
-    s.ulab = g->label_rank(ulabel);
-    bool empty = s.ulab < 0;
-    for (int j = 0; j < d; ++j) {
-        if (col[j] < 0 || col[j] >= t || lab[j] < 0) {
-            set_error("gsi_join_step: column out of range or negative label");
-            return GSI_EINVAL;
-        }
-        s.col[j] = col[j];
-        s.lab[j] = lab[j];
-        empty |= lab[j] >= g->L;
-    }
-    for (int c = 0; c <= t; ++c) s.perm[c] = c;
-    *count = 0;
-    if (R == 0 || empty) return GSI_OK;
+    bool empty = false;
+    GSI_TRY(join_step_args("gsi_join_step", g, M, R, t, cand, ulabel, col, lab, d, out, out_cap, count, &s, &empty));
+    if (empty) return GSI_OK;
     GSI_TRY(prepare_device(g->device));
     cudaStream_t st = (cudaStream_t)stream;
     uint64_t *F = nullptr, *scr = nullptr;

@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "runtime.h"
 #include "scan.cuh"
 
 namespace gsi {
@@ -76,14 +77,11 @@ extern "C" gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint
                                             const uint32_t *cand, int32_t ulabel, const int32_t *col,
                                             const int32_t *lab, int32_t d, int32_t *out, uint64_t out_cap,
                                             uint64_t *count, void *stream) {
-    if (!g || !count || !col || !lab || (R > 0 && (!M || !cand)) || (out_cap > 0 && !out)) {
-        set_error("gsi_join_step_noalloc: null argument");
-        return GSI_EINVAL;
-    }
-    if (t < 1 || t >= GSI_MAX_QUERY_VERTICES || d < 1 || d > t) {
-        set_error("gsi_join_step_noalloc: need 1 <= d <= t < 32");
-        return GSI_EINVAL;
-    }
+    GSI_API_BEGIN
+    JoinStep s;
+    bool empty = false;
+    GSI_TRY(join_step_args("gsi_join_step_noalloc", g, M, R, t, cand, ulabel, col, lab, d, out, out_cap, count, &s,
+                           &empty));
     if (R > NA_MAX_ROWS) {
         set_error("gsi_join_step_noalloc: more than 2^20 input rows (the static scratch limit)");
         return GSI_EINVAL;
@@ -92,23 +90,7 @@ extern "C" gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint
         set_error("gsi_join_step_noalloc: scan scratch larger than the static array");
         return GSI_EINVAL;
     }
-    JoinStep s;
-    s.t = t;
-    s.d = d;
-    s.ulab = g->label_rank(ulabel);
-    bool empty = s.ulab < 0;
-    for (int j = 0; j < d; ++j) {
-        if (col[j] < 0 || col[j] >= t || lab[j] < 0) {
-            set_error("gsi_join_step_noalloc: column out of range or negative label");
-            return GSI_EINVAL;
-        }
-        s.col[j] = col[j];
-        s.lab[j] = lab[j];
-        empty |= lab[j] >= g->L;
-    }
-    for (int c = 0; c <= t; ++c) s.perm[c] = c;
-    *count = 0;
-    if (R == 0 || empty) return GSI_OK;
+    if (empty) return GSI_OK;
 
     GSI_CUDA_TRY(cudaSetDevice(g->device));
     (void)cudaGetLastError();
@@ -136,4 +118,5 @@ extern "C" gsi_status gsi_join_step_noalloc(gsi_graph *g, const int32_t *M, uint
     GSI_CUDA_TRY(cudaStreamSynchronize(st));
     *count = h;
     return GSI_OK;
+    GSI_API_END
 }

@@ -193,5 +193,13 @@ void plan_order(const QueryGraph &q, const uint64_t *cand, const uint64_t *freq,
 void make_steps(const QueryGraph &q, const int32_t *order, const int32_t *first, const int32_t *ranks,
                 std::vector<JoinStep> &steps);
 gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o, gsi_result **out);
+// Argument checks of one join-step call (gsi_join_step and its allocation-free
+// variant; `who` prefixes the error message).  Fills s with the step (output
+// columns in input order, every column tested by the set subtraction), sets
+// *count = 0 and *empty when no row can have a survivor (no rows, or a label
+// no data vertex or edge carries).
+gsi_status join_step_args(const char *who, gsi_graph *g, const int32_t *M, uint64_t R, int32_t t,
+                          const uint32_t *cand, int32_t ulabel, const int32_t *col, const int32_t *lab, int32_t d,
+                          int32_t *out, uint64_t out_cap, uint64_t *count, JoinStep *s, bool *empty);
 
 }  // namespace gsi
