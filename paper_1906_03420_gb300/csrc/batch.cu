@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "join_rows.cuh"
 #include "join_tile.cuh"
 #include "runtime.h"
 
@@ -136,11 +137,14 @@ __device__ long long next_unit(const BatchArgs &b) {
     }
 }
 
-__global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(BNT, 4) k_batch(const __grid_constant__ BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long wt[BNT / 32];
     __shared__ long long unit_s;
-    __shared__ unsigned long long cnt_s, off_s, slot_s;
+    __shared__ unsigned long long cnt_s, lcnt_s, off_s, slot_s;
+    __shared__ unsigned rfail_s;
     __shared__ int fail_s, skip_s;
+    __shared__ __align__(16) JoinArgs a_s;
     unsigned char *slice = b.arena + (uint64_t)blockIdx.x * b.slice_bytes;
     uint64_t *S = reinterpret_cast<uint64_t *>(slice);
     int32_t *reg[2] = {reinterpret_cast<int32_t *>(slice + b.s_bytes),
@@ -200,65 +204,76 @@ __global__ void __launch_bounds__(BNT) k_batch(const __grid_constant__ BatchArgs
         bool failed = false;
         uint64_t cap = 0;
         for (int t = t0; t < k && R > 0 && !skip; ++t) {
-            const JoinArgs &a = b.cfgs[bq->cfg0 + t];
+            __syncthreads();                      // the previous step's readers of a_s are done
+            {   // this step's configuration in shared memory
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(b.cfgs + bq->cfg0 + t);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&a_s);
+                for (int i = threadIdx.x; i < (int)(sizeof(JoinArgs) / 4); i += BNT) dst[i] = src[i];
+            }
+            const JoinArgs &a = a_s;
             int32_t *out = reg[oreg];
-            if ((R + 1) * 8 + R * 8 + 64 > S_words * 8) { failed = true; break; }
-            uint64_t *F = S;
-            uint32_t *bnd = reinterpret_cast<uint32_t *>(S + S_words) - R;   // bound records (see join_tile)
-            uint32_t *blo = bnd - R;
-            // bounds and slot offsets (CTA-local scan)
-            unsigned long long run = 0, abytes = 0;
-            bool too_long = false;
-            for (uint64_t base = 0; base < R; base += BNT) {
-                const uint64_t i = base + threadIdx.x;
-                unsigned long long v = 0;
-                if (i < R) {
-                    uint32_t lob;
-                    int jb;
-                    uint64_t lsum;
-                    const uint32_t c = row_bound_full(a.s, M + i * (uint64_t)a.s.t, a.off, a.cl, &lob, &jb, &lsum);
-                    if (a.stats) abytes += row_alg_bytes(a.s.t, a.s.d, lsum, c);
-                    too_long |= c > BOUND_LEN_MASK;
-                    bnd[i] = (c & BOUND_LEN_MASK) | ((uint32_t)jb << BOUND_LEN_BITS);
-                    blo[i] = lob;
-                    v = (unsigned long long)c + W;
-                }
-                unsigned long long tot;
-                const unsigned long long ex = block_exclusive_scan<BNT, unsigned long long>(v, wt, &tot) + run;
-                if (i < R) F[i] = ex;
-                run += tot;
-            }
-            const uint64_t total = run;
-            if (__syncthreads_or(too_long)) { failed = true; break; }   // record too small: the plain path
-            if (a.stats) {                       // one add per step of a unit
-                abytes = block_sum<BNT, unsigned long long>(abytes, wt);
-                if (threadIdx.x == 0) {
-                    if (abytes) atomicAdd(a.stats, abytes);
-                    atomicAdd(a.stats + 1, (unsigned long long)(total - W * R));
-                }
-            }
-            if (threadIdx.x == 0) {
-                F[R] = total;
-                cnt_s = 0;
-            }
             const bool last = t == k - 1;
             cap = b.t_bytes / (4ull * (uint64_t)(t + 1));
             if (last && bq->count_only) cap = 0;
+            // long rows (bound above SHORT_MAX) and their slot offsets in the scratch region
+            const LongLayout ll = long_layout(S_words, t);
+            LongTable lt;
+            lt.rows = reinterpret_cast<int32_t *>(S);
+            lt.bnd = reinterpret_cast<uint32_t *>(lt.rows + ll.cap * (uint64_t)t);
+            lt.blo = lt.bnd + ll.cap;
+            lt.cap = ll.cap;
+            lt.count = &lcnt_s;
+            uint64_t *F = S + ll.f_off;
+            if (threadIdx.x == 0) {
+                cnt_s = 0;
+                lcnt_s = 0;
+                rfail_s = 0;
+            }
             __syncthreads();
-            // tiles in order; each tile spans at most BNV/W + 1 rows past its first
-            const uint64_t ntiles = (total + BNV - 1) / BNV;
-            int64_t r_lo = 0;
-            const uint64_t span = BNV / W + 1;
-            for (uint64_t tile = 0; tile < ntiles; ++tile) {
-                const uint64_t s_next = min((tile + 1) * (uint64_t)BNV, total);
-                const uint64_t lim = min((uint64_t)R - (uint64_t)r_lo, span);
-                unsigned long long cn = 0;
-                for (uint64_t j = threadIdx.x; j <= lim; j += BNT) cn += F[r_lo + j] <= s_next;
-                cn = block_sum<BNT, unsigned long long>(cn, wt);
-                const int64_t r_next = r_lo + (int64_t)cn - 1;
-                join_tile<BNT, BVT, false, true>(a, M, (int64_t)R, F, total, r_lo, r_next, out, cap, &cnt_s, tile,
-                                                 bnd, blo);
-                r_lo = r_next;
+            // short rows joined inline, long rows set aside
+            unsigned long long abytes = 0, items = 0;
+            row_pass<BNT>(a, M, R, 0, BNT * ROW_RPT, out, cap, &cnt_s, lt, &rfail_s, smem, &abytes, &items);
+            if (a.stats) {                       // one add per step of a unit
+                abytes = block_sum<BNT, unsigned long long>(abytes, wt);
+                items = block_sum<BNT, unsigned long long>(items, wt);
+                if (threadIdx.x == 0) {
+                    if (abytes) atomicAdd(a.stats, abytes);
+                    if (items) atomicAdd(a.stats + 1, items);
+                }
+            }
+            __syncthreads();
+            if (rfail_s) { failed = true; break; }     // long-row table full: the plain path
+            const uint64_t L = lcnt_s;
+            if (L > 0) {
+                // the long rows through the candidate-slot tiles, CTA-local
+                unsigned long long run = 0;
+                for (uint64_t base = 0; base < L; base += BNT) {
+                    const uint64_t i = base + threadIdx.x;
+                    const unsigned long long v =
+                        i < L ? (unsigned long long)(lt.bnd[i] & BOUND_LEN_MASK) + W : 0ull;
+                    unsigned long long tot;
+                    const unsigned long long ex = block_exclusive_scan<BNT, unsigned long long>(v, wt, &tot) + run;
+                    if (i < L) F[i] = ex;
+                    run += tot;
+                }
+                const uint64_t total = run;
+                if (threadIdx.x == 0) F[L] = total;
+                __syncthreads();
+                // tiles in order; each tile spans at most BNV/W + 1 rows past its first
+                const uint64_t ntiles = (total + BNV - 1) / BNV;
+                int64_t r_lo = 0;
+                const uint64_t span = BNV / W + 1;
+                for (uint64_t tile = 0; tile < ntiles; ++tile) {
+                    const uint64_t s_next = min((tile + 1) * (uint64_t)BNV, total);
+                    const uint64_t lim = min(L - (uint64_t)r_lo, span);
+                    unsigned long long cn = 0;
+                    for (uint64_t j = threadIdx.x; j <= lim; j += BNT) cn += F[r_lo + j] <= s_next;
+                    cn = block_sum<BNT, unsigned long long>(cn, wt);
+                    const int64_t r_next = r_lo + (int64_t)cn - 1;
+                    join_tile<BNT, BVT, false, true>(a, lt.rows, (int64_t)L, F, total, r_lo, r_next, out, cap, &cnt_s,
+                                                     tile, lt.bnd, lt.blo);
+                    r_lo = r_next;
+                }
             }
             __syncthreads();
             const uint64_t cnt = cnt_s;
@@ -394,8 +409,10 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
     for (int i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
         if (!p.active) continue;
-        for (int t = 1; t < p.k; ++t)
+        for (int t = 1; t < p.k; ++t) {
             sm = std::max(sm, join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, p.steps[t].t, p.steps[t].d));
+            sm = std::max(sm, rows_smem(BNT, p.steps[t].t));
+        }
     }
     if (sm > 200 * 1024) {
         set_error("batch: shared memory need exceeds 200 KB");

@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cf
         __syncthreads();
         // ---- short rows joined inline, long rows set aside (one pass over M)
         unsigned long long abytes = 0, items = 0;
-        row_pass<NT>(a, st->M, R, (uint64_t)blockIdx.x * NT, (uint64_t)G * NT, st->out, cap, &st->count, lt, &ctl->fail,
-                     smem, &abytes, &items);
+        row_pass<NT>(a, st->M, R, (uint64_t)blockIdx.x * NT * ROW_RPT, (uint64_t)G * NT * ROW_RPT, st->out, cap,
+                     &st->count, lt, &ctl->fail, smem, &abytes, &items);
         if (a.stats) {                       // one add per CTA and step
             abytes = block_sum<NT, unsigned long long>(abytes, wt);
             items = block_sum<NT, unsigned long long>(items, wt);
@@ -370,7 +370,8 @@ gsi_status launch_join_scan(const gsi_graph *g, const int32_t *M, uint64_t R, co
 }
 
 size_t join_smem(int rmax, int t, int d) {
-    return (size_t)(rmax + 1) * 8 + (size_t)rmax * 4 + (size_t)rmax * 2 * (d - 1) * 4 + (size_t)rmax * t * 4;
+    return (size_t)JOIN_NV * 8 + (size_t)(rmax + 1) * 8 + (size_t)rmax * 4 + (size_t)rmax * 2 * (d - 1) * 4 +
+           (size_t)rmax * t * 4 + (size_t)JOIN_NV * 2;
 }
 
 gsi_status launch_partition(const uint64_t *F, uint64_t R, uint64_t total, int64_t *part, cudaStream_t st) {
@@ -459,7 +460,7 @@ gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &s
         cfg[t].memo = memo;
         cfg[t].memo_n = g->n;
         sm = std::max(sm, join_smem(cfg[t].rmax, steps[t].t, steps[t].d));
-        sm = std::max(sm, rows_smem(JOIN_NT, steps[t].t, SHORT_MAX));
+        sm = std::max(sm, rows_smem(JOIN_NT, steps[t].t));
     }
     if (sm > 200 * 1024) {
         set_error("join: shared memory need exceeds 200 KB");

@@ -75,10 +75,27 @@ __host__ __device__ inline LongLayout long_layout(uint64_t S_words, int t) {
     return l;
 }
 
-// Dynamic shared memory of the row pass: NT staged rows of t columns, then
-// the batch's survivors (value, local row).
-__host__ __device__ constexpr size_t rows_smem(int nt, int t, int s) {
-    return (size_t)nt * (size_t)t * 4 + (size_t)nt * (size_t)s * 4 + (size_t)nt * (size_t)s;
+constexpr int ROW_RPT = 2;        // rows per thread in one batch of the row pass
+constexpr int ROW_SURV = 4;       // survivor-list entries per batch row (more are written in rounds)
+
+// Dynamic shared memory of the row pass for CTAs of nt threads: nt * ROW_RPT
+// staged rows of t columns, their candidate sub-list starts, then the
+// survivor list (values, local row and candidate position).
+__host__ __device__ constexpr size_t rows_smem(int nt, int t) {
+    return (size_t)nt * ROW_RPT * ((size_t)t * 4 + 4) + (size_t)nt * ROW_RPT * ROW_SURV * 6;
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (TMA engine, no registers or
+// shared memory involved): the start is rounded up and the size down to 16
+// bytes, so the prefetch never reaches past the range.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint64_t bytes) {
+    const uint64_t a = (uint64_t)reinterpret_cast<uintptr_t>(p);
+    const uint64_t end = (a + bytes) & ~15ull;
+    for (uint64_t x = (a + 15) & ~15ull; x < end;) {
+        const uint32_t chunk = (uint32_t)min(end - x, (uint64_t)1 << 20);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(x), "r"(chunk) : "memory");
+        x += chunk;
+    }
 }
 
 // Start (*lo) and length (returned) of the label(u) sub-list of N(v, lab[j]),
@@ -139,156 +156,298 @@ __device__ __forceinline__ uint32_t subtract_row(const JoinArgs &a, const int32_
     return mask;
 }
 
-// The row pass over rows [first, R) in batches of NT rows, batch starts
-// `stride` apart (a grid-strided pass: first = blockIdx.x * NT, stride =
-// gridDim.x * NT; one CTA alone: first = 0, stride = NT).  `a` should live in
-// shared memory.  Survivors go to out (up to cap rows; `count` is exact),
-// long rows to lt.  Bit 1 of *fail is set when the long-row table is full or
-// a bound does not fit its record.  Adds this thread's algorithmic bytes
-// (rows read, lists located and read; survivors are counted by the caller)
-// and candidate slots to *abytes / *items when a.stats is set.
+// One row of the pass: its bound (shortest label sub-list: length *best,
+// start *lob, linking edge *jb) and the mask of its survivors among the
+// first *best candidates when best <= SHORT_MAX.  Lanes whose rows share the
+// first-edge vertex of a single-edge step share the lookup and the bitmap
+// probes (every lane of the warp must call this together).
+template <bool DR>
+__device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *row, bool valid, int lane,
+                                             uint32_t *best_out, uint32_t *lob_out, int *jb_out,
+                                             unsigned long long *abytes, unsigned long long *items) {
+    const int t = a.s.t, d = a.s.d;
+    const bool stats = a.stats != nullptr;
+    uint32_t mask = 0, best = 0, lob = 0;
+    int jb = 0;
+    if (DR && d == 1) {
+        const int32_t v = valid ? row[a.s.col[0]] : -1 - lane;
+        const unsigned peers = __match_any_sync(FULL_MASK, v);
+        const int leader = __ffs(peers) - 1;
+        uint32_t bm = 0;
+        if (lane == leader && valid) {
+            best = sublist(a, 0, v, &lob);
+            if (best <= (uint32_t)SHORT_MAX) bm = bitmap_mask(a, lob, best);
+        }
+        best = __shfl_sync(FULL_MASK, best, leader);
+        lob = __shfl_sync(FULL_MASK, lob, leader);
+        bm = __shfl_sync(FULL_MASK, bm, leader);
+        if (valid && best <= (uint32_t)SHORT_MAX) mask = subtract_row(a, row, lob, bm);
+        if (valid && stats) {
+            *abytes += row_alg_bytes(t, 1, best, best);
+            *items += best;
+        }
+    } else if (valid) {
+        uint32_t lo4[MEMO_EDGES], len4[MEMO_EDGES];
+        uint64_t lsum = 0;
+        best = 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < MEMO_EDGES; ++j) {
+            lo4[j] = 0;
+            len4[j] = 0;
+            if (j < d) {
+                len4[j] = sublist(a, j, row[a.s.col[j]], &lo4[j]);
+                lsum += len4[j];
+                if (len4[j] < best) {
+                    best = len4[j];
+                    lob = lo4[j];
+                    jb = j;
+                }
+            }
+        }
+        for (int j = MEMO_EDGES; j < d; ++j) {
+            uint32_t l;
+            const uint32_t n = sublist(a, j, row[a.s.col[j]], &l);
+            lsum += n;
+            if (n < best) {
+                best = n;
+                lob = l;
+                jb = j;
+            }
+        }
+        if (stats) {
+            *abytes += row_alg_bytes(t, d, lsum, best);
+            *items += best;
+        }
+        if (best > 0 && best <= (uint32_t)SHORT_MAX) {
+            mask = subtract_row(a, row, lob, bitmap_mask(a, lob, best));
+            // every other linking list must hold the candidate (Alg. 3)
+            for (uint32_t m = mask; m; m &= m - 1) {
+                const int p = __ffs(m) - 1;
+                const int32_t w = __ldg(a.ci + lob + (uint32_t)p);
+                bool ok = true;
+#pragma unroll
+                for (int j = 0; j < MEMO_EDGES; ++j)
+                    if (ok && j < d && j != jb) ok = sorted_contains(a.ci + lo4[j], len4[j], w);
+                for (int j = MEMO_EDGES; j < d && ok; ++j) {
+                    if (j == jb) continue;
+                    const uint64_t seg =
+                        (uint64_t)(uint32_t)row[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+                    ok = ranked_contains(a.ci, a.cl, __ldg(a.off + seg), __ldg(a.off + seg + 1),
+                                         (uint32_t)a.s.ulab, w);
+                }
+                if (!ok) mask &= ~(1u << p);
+            }
+        }
+    }
+    *best_out = best;
+    *lob_out = lob;
+    *jb_out = jb;
+    return mask;
+}
+
+// The single-edge rows of one thread (RPT of them, rows q * NT + tid) in
+// lockstep, so that each round of loads is issued for all of them at once:
+// first-edge vertices and their warp groups, memo lookups (the leader of each
+// group), candidate values, bitmap probes, then the group's bound and bitmap
+// mask to every lane, and each lane's own set subtraction.  Sets best[q],
+// lob[q] and mask[q]; rows past nb get best 0.
+constexpr int ROW_C = 8;          // candidate values of a single-edge group loaded in the first round
+
+template <int NT, int RPT>
+__device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_t *rowv, int nb, int lane,
+                                                 uint32_t *best, uint32_t *lob, uint32_t *mask,
+                                                 unsigned long long *abytes, unsigned long long *items) {
+    constexpr int C = ROW_C;
+    const int t = a.s.t;
+    int32_t v[RPT];
+    bool lead[RPT];
+    int leader[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int lr = q * NT + (int)threadIdx.x;
+        v[q] = lr < nb ? rowv[lr * t + a.s.col[0]] : -1 - lane;
+        const unsigned peers = __match_any_sync(FULL_MASK, v[q]);
+        leader[q] = __ffs(peers) - 1;
+        lead[q] = lane == leader[q] && lr < nb;
+    }
+    // memo lookups of the group leaders
+    uint64_t e[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+        e[q] = (lead[q] && a.memo) ? a.memo[(uint32_t)v[q]] : 0ull;
+    uint32_t len[RPT], lo[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        len[q] = 0;
+        lo[q] = 0;
+        if (!lead[q]) continue;
+        if (a.memo && (uint32_t)(e[q] >> MEMO_TAG_SHIFT) == (uint32_t)a.s.t) {
+            lo[q] = (uint32_t)e[q];
+            len[q] = (uint32_t)(e[q] >> 32) & BOUND_LEN_MASK;
+        } else {
+            len[q] = sublist(a, 0, v[q], &lo[q]);
+        }
+    }
+    // the first C candidates of every short group, then their bitmap probes
+    int32_t w[RPT][C];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int p = 0; p < C; ++p)
+            w[q][p] = (lead[q] && (uint32_t)p < len[q] && len[q] <= (uint32_t)SHORT_MAX)
+                          ? __ldg(a.ci + lo[q] + (uint32_t)p) : -1;
+    uint32_t bm[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        bm[q] = 0;
+#pragma unroll
+        for (int p = 0; p < C; ++p)
+            if (w[q][p] >= 0 && ((__ldg(a.cand + (w[q][p] >> 5)) >> (w[q][p] & 31)) & 1u)) bm[q] |= 1u << p;
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)                     // candidates past the first C (groups with C < len <= SHORT_MAX)
+        if (lead[q] && len[q] > (uint32_t)C && len[q] <= (uint32_t)SHORT_MAX)
+            bm[q] |= bitmap_mask(a, lo[q] + C, len[q] - C) << C;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int lr = q * NT + (int)threadIdx.x;
+        const bool valid = lr < nb;
+        best[q] = __shfl_sync(FULL_MASK, len[q], leader[q]);
+        lob[q] = __shfl_sync(FULL_MASK, lo[q], leader[q]);
+        const uint32_t b = __shfl_sync(FULL_MASK, bm[q], leader[q]);
+        if (!valid) best[q] = 0;
+        mask[q] = (valid && best[q] <= (uint32_t)SHORT_MAX) ? subtract_row(a, rowv + lr * t, lob[q], b) : 0u;
+        if (valid && a.stats) {
+            *abytes += row_alg_bytes(t, 1, best[q], best[q]);
+            *items += best[q];
+        }
+    }
+}
+
+// The row pass over rows [first, R) in batches of NT * ROW_RPT rows, batch
+// starts `stride` apart (a grid-strided pass: first = blockIdx.x * NB,
+// stride = gridDim.x * NB; one CTA alone: first = 0, stride = NB).  `a` should
+// live in shared memory.  Survivors go to out (up to cap rows; `count` is
+// exact), long rows to lt.  Bit 1 of *fail is set when the long-row table is
+// full or a bound does not fit its record.  Adds this thread's algorithmic
+// bytes (rows read, lists located and read; survivors are counted by the
+// caller) and candidate slots to *abytes / *items when a.stats is set.
 template <int NT, bool DR = true>
 __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64_t first, uint64_t stride,
                          int32_t *__restrict__ out, uint64_t cap, unsigned long long *count, const LongTable &lt,
                          unsigned *fail, unsigned char *smem, unsigned long long *abytes,
                          unsigned long long *items) {
-    constexpr int NW = NT / 32;
+    constexpr int NW = NT / 32, NB = NT * ROW_RPT, CCAP = NB * ROW_SURV;
     __shared__ uint32_t wt[NW];
     __shared__ unsigned long long base_s, lbase_s;
-    const int t = a.s.t, d = a.s.d, W1 = t + 1;
+    const int t = a.s.t, W1 = t + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t *rowv = reinterpret_cast<int32_t *>(smem);                  // NT * t
-    int32_t *comp_w = rowv + NT * t;                                    // NT * SHORT_MAX
-    uint8_t *comp_r = reinterpret_cast<uint8_t *>(comp_w + NT * SHORT_MAX);
-    const bool stats = a.stats != nullptr;
+    int32_t *rowv = reinterpret_cast<int32_t *>(smem);                  // NB * t
+    uint32_t *lobs = reinterpret_cast<uint32_t *>(rowv + NB * t);        // NB
+    int32_t *comp_w = reinterpret_cast<int32_t *>(lobs + NB);           // CCAP
+    uint16_t *comp_r = reinterpret_cast<uint16_t *>(comp_w + CCAP);     // local row | position << 10
     const bool write = cap > 0;
     // the output loop's fixed lane map: lane = rs * W1 + c writes column c of
     // the rs-th of the warp's rpw rows per round
     const int rpw = 32 / W1, rs = lane / W1, oc = lane - rs * W1;
     const int src_col = a.iperm[oc < W1 ? oc : 0];
     for (uint64_t r0 = first; r0 < R; r0 += stride) {
-        const int nb = (int)min((uint64_t)NT, R - r0);
+        const int nb = (int)min((uint64_t)NB, R - r0);
         const int32_t *src = M + r0 * (uint64_t)t;
+        if (threadIdx.x == 0 && r0 + stride < R)      // the next batch's rows, while this one runs
+            prefetch_l2(M + (r0 + stride) * (uint64_t)t, min((uint64_t)NB, R - r0 - stride) * (uint64_t)t * 4);
         for (int e = threadIdx.x; e < nb * t; e += NT) rowv[e] = __ldcg(src + e);
         __syncthreads();
-        const bool valid = threadIdx.x < nb;
-        const int32_t *row = rowv + (valid ? threadIdx.x : 0) * t;
-        uint32_t mask = 0, best = 0, lob = 0;
-        int jb = 0;
-        if (DR && d == 1) {
-            // rows of the warp that share the first-edge vertex share its
-            // sub-list and bitmap probes: one lane works for the group
-            const int32_t v = valid ? row[a.s.col[0]] : -1 - lane;
-            const unsigned peers = __match_any_sync(FULL_MASK, v);
-            const int leader = __ffs(peers) - 1;
-            uint32_t bm = 0;
-            if (lane == leader && valid) {
-                best = sublist(a, 0, v, &lob);
-                if (best <= (uint32_t)SHORT_MAX) bm = bitmap_mask(a, lob, best);
-            }
-            best = __shfl_sync(FULL_MASK, best, leader);
-            lob = __shfl_sync(FULL_MASK, lob, leader);
-            bm = __shfl_sync(FULL_MASK, bm, leader);
-            if (valid && best <= (uint32_t)SHORT_MAX) mask = subtract_row(a, row, lob, bm);
-            if (valid && stats) {
-                *abytes += row_alg_bytes(t, 1, best, best);
-                *items += best;
-            }
-        } else if (valid) {
-            // the shortest label sub-list over the linking edges
-            uint32_t lo4[MEMO_EDGES], len4[MEMO_EDGES];
-            uint64_t lsum = 0;
-            best = 0xffffffffu;
+        // this thread's rows q * NT + tid, q < ROW_RPT (a warp's lanes hold
+        // consecutive rows)
+        uint32_t mask[ROW_RPT], best[ROW_RPT], lob[ROW_RPT];
+        int jb[ROW_RPT];
+        uint32_t n = 0, nl = 0;
+        if (DR && a.s.d == 1) {
+            rows_join_single<NT, ROW_RPT>(a, rowv, nb, lane, best, lob, mask, abytes, items);
 #pragma unroll
-            for (int j = 0; j < MEMO_EDGES; ++j) {
-                lo4[j] = 0;
-                len4[j] = 0;
-                if (j < d) {
-                    len4[j] = sublist(a, j, row[a.s.col[j]], &lo4[j]);
-                    lsum += len4[j];
-                    if (len4[j] < best) {
-                        best = len4[j];
-                        lob = lo4[j];
-                        jb = j;
-                    }
-                }
-            }
-            for (int j = MEMO_EDGES; j < d; ++j) {
-                uint32_t l;
-                const uint32_t n = sublist(a, j, row[a.s.col[j]], &l);
-                lsum += n;
-                if (n < best) {
-                    best = n;
-                    lob = l;
-                    jb = j;
-                }
-            }
-            if (stats) {
-                *abytes += row_alg_bytes(t, d, lsum, best);
-                *items += best;
-            }
-            if (best > 0 && best <= (uint32_t)SHORT_MAX) {
-                mask = subtract_row(a, row, lob, bitmap_mask(a, lob, best));
-                // every other linking list must hold the candidate (Alg. 3)
-                for (uint32_t m = mask; m; m &= m - 1) {
-                    const int p = __ffs(m) - 1;
-                    const int32_t w = __ldg(a.ci + lob + (uint32_t)p);
-                    bool ok = true;
+            for (int q = 0; q < ROW_RPT; ++q) jb[q] = 0;
+        } else {
 #pragma unroll
-                    for (int j = 0; j < MEMO_EDGES; ++j)
-                        if (ok && j < d && j != jb) ok = sorted_contains(a.ci + lo4[j], len4[j], w);
-                    for (int j = MEMO_EDGES; j < d && ok; ++j) {
-                        if (j == jb) continue;
-                        const uint64_t seg =
-                            (uint64_t)(uint32_t)row[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
-                        ok = ranked_contains(a.ci, a.cl, __ldg(a.off + seg), __ldg(a.off + seg + 1),
-                                             (uint32_t)a.s.ulab, w);
-                    }
-                    if (!ok) mask &= ~(1u << p);
-                }
+            for (int q = 0; q < ROW_RPT; ++q) {
+                const int lr = q * NT + (int)threadIdx.x;
+                const bool valid = lr < nb;
+                mask[q] = row_join<false>(a, rowv + (valid ? lr : 0) * t, valid, lane, &best[q], &lob[q], &jb[q],
+                                          abytes, items);
+                if (!valid) best[q] = 0;
             }
         }
-        const bool lng = valid && best > (uint32_t)SHORT_MAX;
-        const uint32_t n = __popc(mask);
+#pragma unroll
+        for (int q = 0; q < ROW_RPT; ++q) {
+            n += __popc(mask[q]);
+            nl += best[q] > (uint32_t)SHORT_MAX;
+        }
         uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<NT, uint32_t>(n | ((uint32_t)lng << 16), wt, &tot);
+        const uint32_t ex = block_exclusive_scan<NT, uint32_t>(n | (nl << 16), wt, &tot);
         const uint32_t ntot = tot & 0xffffu, ltot = tot >> 16;
         if (threadIdx.x == 0) {
             base_s = ntot ? atomicAdd(count, (unsigned long long)ntot) : 0ull;
             lbase_s = ltot ? atomicAdd(lt.count, (unsigned long long)ltot) : 0ull;
         }
-        if (write && mask) {                 // survivors to their place in the batch's run
-            uint32_t i = ex & 0xffffu;
-            for (uint32_t m = mask; m; m &= m - 1) {
-                comp_w[i] = __ldg(a.ci + lob + (uint32_t)(__ffs(m) - 1));
-                comp_r[i] = (uint8_t)threadIdx.x;
-                ++i;
-            }
-        }
         __syncthreads();
-        if (lng) {
-            const unsigned long long li = lbase_s + (ex >> 16);
-            if (li < lt.cap && best <= BOUND_LEN_MASK) {
-                int32_t *dst = lt.rows + li * (uint64_t)t;
-                for (int c = 0; c < t; ++c) dst[c] = row[c];
-                lt.bnd[li] = best | ((uint32_t)jb << BOUND_LEN_BITS);
-                lt.blo[li] = lob;
-            } else {
-                atomicOr(fail, 1u);
+        // long rows to the table
+        {
+            unsigned long long li = lbase_s + (ex >> 16);
+#pragma unroll
+            for (int q = 0; q < ROW_RPT; ++q) {
+                if (best[q] <= (uint32_t)SHORT_MAX) continue;
+                const int32_t *row = rowv + (q * NT + (int)threadIdx.x) * t;
+                if (li < lt.cap && best[q] <= BOUND_LEN_MASK) {
+                    int32_t *dst = lt.rows + li * (uint64_t)t;
+                    for (int c = 0; c < t; ++c) dst[c] = row[c];
+                    lt.bnd[li] = best[q] | ((uint32_t)jb[q] << BOUND_LEN_BITS);
+                    lt.blo[li] = lob[q];
+                } else {
+                    atomicOr(fail, 1u);
+                }
+                ++li;
             }
         }
-        if (write && ntot) {
-            const uint64_t base = base_s;
-            const uint64_t room = cap > base ? cap - base : 0;
-            const uint32_t nrow = (uint32_t)min((uint64_t)ntot, room);
-            int32_t *dst = out + base * (uint64_t)W1;
+        if (!write || ntot == 0) {
+            __syncthreads();
+            continue;
+        }
+        // survivors in rounds of CCAP rows: list, then one coalesced run
+        const uint64_t base = base_s;
+        const uint64_t room = cap > base ? cap - base : 0;
+        const uint32_t nrow = (uint32_t)min((uint64_t)ntot, room);
+        for (uint32_t rb = 0; rb < nrow; rb += CCAP) {
+            const uint32_t re = min(nrow, rb + (uint32_t)CCAP);
+            // each thread lists its survivors as (local row, candidate
+            // position); the values are then fetched with the loads spread
+            // over all threads instead of one serial chain per thread
+            uint32_t i = ex & 0xffffu;
+#pragma unroll
+            for (int q = 0; q < ROW_RPT; ++q) {
+                const int lr = q * NT + (int)threadIdx.x;
+                if (rb == 0 && mask[q]) lobs[lr] = lob[q];
+                for (uint32_t m = mask[q]; m && i < re; m &= m - 1) {
+                    if (i >= rb) comp_r[i - rb] = (uint16_t)(lr | ((__ffs(m) - 1) << 10));
+                    ++i;
+                }
+            }
+            __syncthreads();
+            const uint32_t nr0 = re - rb;
+            for (uint32_t r = threadIdx.x; r < nr0; r += NT) {
+                const uint32_t e = comp_r[r];
+                comp_w[r] = __ldg(a.ci + lobs[e & 1023u] + (e >> 10));
+            }
+            __syncthreads();
+            int32_t *dst = out + (base + rb) * (uint64_t)W1;
+            const uint32_t nr = re - rb;
             if (rs < rpw)
-                for (uint32_t r = (uint32_t)(warp * rpw + rs); r < nrow; r += (uint32_t)(NW * rpw)) {
-                    const int32_t val = src_col == t ? comp_w[r] : rowv[(int)comp_r[r] * t + src_col];
+                for (uint32_t r = (uint32_t)(warp * rpw + rs); r < nr; r += (uint32_t)(NW * rpw)) {
+                    const int32_t val = src_col == t ? comp_w[r] : rowv[(int)(comp_r[r] & 1023u) * t + src_col];
                     dst[(uint64_t)r * W1 + oc] = val;
                 }
+            __syncthreads();
         }
-        __syncthreads();
+        if (nrow == 0) __syncthreads();
     }
 }
 

@@ -180,15 +180,18 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
     __shared__ unsigned long long wt[NT / 32];
     __shared__ int wti[NT / 32];
     __shared__ unsigned long long gbase_s;
-    __shared__ uint16_t rowmap[NV];
-    __shared__ int2 wsurv[NT / 32][32 * VT];          // per-warp survivors (local row, w)
     __shared__ unsigned wcnt[NT / 32 + 1];
 
     const int t = a.s.t, d = a.s.d, dm1 = d - 1;
-    uint64_t *Fs = reinterpret_cast<uint64_t *>(smem);                 // rmax + 1
+    // dynamic shared memory (join_smem): per-warp survivors (local row, w),
+    // row offsets, candidate sub-list starts, other lists, staged rows, and
+    // the slot -> row map
+    int2 (*wsurv)[32 * VT] = reinterpret_cast<int2 (*)[32 * VT]>(smem);  // NT / 32 warps
+    uint64_t *Fs = reinterpret_cast<uint64_t *>(smem + (size_t)NV * 8);  // rmax + 1
     uint32_t *base0 = reinterpret_cast<uint32_t *>(Fs + a.rmax + 1);    // rmax
     uint32_t *lst = base0 + a.rmax;                                     // rmax * 2 * dm1
     int32_t *rowv = reinterpret_cast<int32_t *>(lst + (size_t)a.rmax * 2 * dm1);   // rmax * t
+    uint16_t *rowmap = reinterpret_cast<uint16_t *>(rowv + (size_t)a.rmax * t);   // NV
 
     // rows r_lo .. min(r_next, R-1): r_lo holds slot s0, r_next holds slot s0 + NV
     const uint64_t s0 = tile * NV;
@@ -335,19 +338,17 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         const uint64_t base = gbase_s + wcnt[warp];
         const uint64_t room = out_cap > base ? out_cap - base : 0;
         const unsigned nrow = (unsigned)min((uint64_t)nw, room);
+        // fixed lane map: lane = rs * W1 + oc writes column oc of the rs-th of
+        // rpw rows per round, so each round stores one contiguous run
         const int W1 = t + 1;
-        const unsigned nel = nrow * (unsigned)W1;
+        const int rpw = 32 / W1, rs = lane / W1, oc = lane - rs * W1;
+        const int c = a.iperm[oc];
         int32_t *dst = out + base * (uint64_t)W1;
-        int row = lane / W1, colx = lane % W1;
-        const int qrow = 32 / W1, qcol = 32 % W1;
-        for (unsigned e = lane; e < nel; e += 32) {
-            const int2 sv = wsurv[warp][row];
-            const int c = a.iperm[colx];
-            dst[e] = c == t ? sv.y : rowv[sv.x * t + c];
-            row += qrow;
-            colx += qcol;
-            if (colx >= W1) { colx -= W1; ++row; }
-        }
+        if (rs < rpw)
+            for (unsigned r = (unsigned)rs; r < nrow; r += (unsigned)rpw) {
+                const int2 sv = wsurv[warp][r];
+                dst[(uint64_t)r * W1 + oc] = c == t ? sv.y : rowv[sv.x * t + c];
+            }
     }
     if (TILE_STATS && a.stats) {
         bytes += 8ull * items;                                    // list element + bitmap probe
