@@ -19,10 +19,11 @@ Workload recipes (``workload(name)``) fix every seed:
                (walk edges plus induced edges up to |E| = 2k).
 * ``scale``    R-MAT scale 24, 256M edges, 256 Zipf vertex labels, 16 edge
                labels; 20 queries with k ~ U{8..16}.
-* ``batched``  the medium graph; 4,096 queries with k ~ U{4..7}.
+* ``batched``  the medium graph; 4,096 queries with k ~ U{4..16}, rare-label
+               walks (below).
 * ``served``   R-MAT scale 22, 64M edges, 128 Zipf vertex labels, 8 edge
-               labels; 20,000 queries, k = 4 + Geometric(mean 2) clipped to
-               [4, 7], Poisson arrivals.
+               labels; 20,000 queries, k = 4 + Geometric(mean 4) clipped to
+               [4, 16] (mean 8), rare-label walks, Poisson arrivals.
 * ``edge``     Erdos-Renyi n=2^20, m=4M (degree at most a few dozen, so its
                line graph stays small: 4M vertices, about 30M edges); 4
                uniform vertex labels, 2 uniform edge labels; 100 random-walk
@@ -37,9 +38,13 @@ workload therefore carries an admission bound: a walk whose labelled
 spanning-tree homomorphism count (an upper bound on its embedding count)
 exceeds ``max_bound`` is redrawn with the next attempt counter.  This is a
 deterministic stand-in for the paper's 100 s per-query timeout.  On these
-graphs almost no walk of 8 or more vertices passes 10^6 (the median bound of
-a 10-vertex walk is about 4e11), so the batched and served workloads, which
-stand for many small requests, draw sizes in 4..7.
+graphs almost no uniform walk of 8 or more vertices passes 10^6 (the median
+bound of a 10-vertex walk is about 4e11), so the batched and served
+workloads, which stand for many small requests of 4..16 vertices, draw
+rare-label walks: the walk starts at and steps to vertices whose label is 8
+or above only (outside the eight most frequent Zipf labels, about 60% of the
+vertices), as most labels of a real labelled graph are rare.  Such walks pass
+the 10^6 bound within a few attempts at every size.
 """
 from __future__ import annotations
 
@@ -86,8 +91,9 @@ def _load():
         lib.synth_adj_degree.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         lib.synth_adj_degree.restype = ctypes.c_int64
         lib.synth_walk_query.argtypes = [ctypes.c_void_p, i32p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
-                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
-                                         i32p, i32p, i32p, ctypes.POINTER(ctypes.c_double)]
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, i32p, i32p, i32p, i32p, i32p,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
         lib.synth_walk_query.restype = ctypes.c_int32
         lib.synth_shape_query.argtypes = [ctypes.c_void_p, i32p, ctypes.c_uint64, ctypes.c_int32,
                                           i32p, i32p, i32p, i32p, i32p]
@@ -157,6 +163,7 @@ class Query:
     occurrence: np.ndarray    # int32[k]: data vertices of one occurrence in G
     dense: bool = False
     bound: float = 0.0        # spanning-tree homomorphism bound (0 if not computed)
+    attempts: int = 1         # walks drawn until this one was admitted
 
     @property
     def k(self) -> int:
@@ -205,10 +212,11 @@ def make_graph(vlab, src, dst, elab, n_elabels, name="") -> Graph:
 
 
 def walk_query(g: Graph, seed: int, index: int, k: int, dense: bool, max_bound: float = 0.0,
-               max_attempts: int = 0) -> Query:
+               max_attempts: int = 0, min_label: int = 0) -> Query:
     """Random-walk query; with max_bound > 0, walks whose labelled spanning-tree
     homomorphism count (an upper bound on the embedding count) exceeds
-    max_bound are redrawn."""
+    max_bound are redrawn.  With min_label > 0 the walk starts at and steps to
+    vertices labelled min_label or above only (a rare-label walk)."""
     lib = _load()
     qvlab = np.empty(k, np.int32)
     cap = max(2 * k, k * (k - 1) // 2) + 1
@@ -217,12 +225,14 @@ def walk_query(g: Graph, seed: int, index: int, k: int, dense: bool, max_bound: 
     qelab = np.empty(cap, np.int32)
     occ = np.empty(k, np.int32)
     bound = ctypes.c_double(0.0)
+    attempts = ctypes.c_int32(0)
     ne = lib.synth_walk_query(g.adj(), _p(g.vlab), seed, index, k, int(dense), float(max_bound), 1,
-                              int(max_attempts), _p(qvlab), _p(qsrc), _p(qdst), _p(qelab), _p(occ),
-                              ctypes.byref(bound))
+                              int(max_attempts), int(min_label), _p(qvlab), _p(qsrc), _p(qdst), _p(qelab), _p(occ),
+                              ctypes.byref(bound), ctypes.byref(attempts))
     if ne < 0:
         raise RuntimeError(f"walk_query: no admissible walk reached {k} vertices")
-    return Query(qvlab, qsrc[:ne].copy(), qdst[:ne].copy(), qelab[:ne].copy(), occ, dense, bound.value)
+    return Query(qvlab, qsrc[:ne].copy(), qdst[:ne].copy(), qelab[:ne].copy(), occ, dense, bound.value,
+                 int(attempts.value))
 
 
 def tree_hom_bound(g: Graph, q: Query) -> float:
@@ -279,6 +289,8 @@ class WorkloadSpec:
     row_cap: int = 0          # 0 = no cap on materialised rows
     max_bound: float = 0.0    # admission bound on the spanning-tree homomorphism count
     description: str = ""
+    min_label: int = 0        # > 0: queries of rare_from_k or more vertices are rare-label walks
+    rare_from_k: int = 0      #      (vertices labelled min_label or above only)
 
 
 GRAPHS = {
@@ -297,10 +309,13 @@ WORKLOADS = {
     "scale": WorkloadSpec("scale", GRAPHS["rmat24"], 20, 8, 16, "uniform", 2003, row_cap=1_000_000_000,
                           max_bound=1e10,
                           description="R-MAT 2^24 / 256M edges, 256 Zipf vlabels, 16 elabels, 20 queries k=8..16"),
-    "batched": WorkloadSpec("batched", GRAPHS["rmat20"], 4096, 4, 7, "uniform", 2004, max_bound=1e6,
-                            description="R-MAT 2^20 graph, 4096 walk queries k=4..16"),
-    "served": WorkloadSpec("served", GRAPHS["rmat22"], 20000, 4, 7, "geometric", 2005, max_bound=1e6,
-                           description="R-MAT 2^22 / 64M edges, 20000 walk queries k=4+Geom (mean 8)"),
+    "batched": WorkloadSpec("batched", GRAPHS["rmat20"], 4096, 4, 16, "uniform", 2004, max_bound=1e6,
+                            description="R-MAT 2^20 graph, 4096 rare-label walk queries k=4..16",
+                            min_label=8, rare_from_k=4),
+    "served": WorkloadSpec("served", GRAPHS["rmat22"], 20000, 4, 16, "geometric", 2005, max_bound=1e6,
+                           description="R-MAT 2^22 / 64M edges, 20000 rare-label walk queries k=4+Geom (mean 8), "
+                                       "clipped to 16",
+                           min_label=8, rare_from_k=4),
     "edge": WorkloadSpec("edge", GRAPHS["er20"], 100, 4, 8, "uniform", 2006, max_bound=1e7,
                          description="ER 2^20 / 4M edges, 4 vlabels, 2 elabels, 100 walk queries k=4..8 "
                                      "asked as edge-isomorphism queries"),
@@ -330,9 +345,10 @@ def graph(name: str) -> Graph:
 
 def query_size(w: WorkloadSpec, i: int) -> int:
     if w.k_dist == "geometric":
-        # k = 4 + G, G geometric on {0,1,...} with mean 2 (p = 1/3), clipped to k_hi
+        # k = 4 + G, G geometric on {0,1,...} with mean 4 (p = 1/5), so that k
+        # has mean 8, clipped to k_hi
         u = unit(w.query_seed, 7, i)
-        p = 1.0 / 3.0
+        p = 1.0 / 5.0
         g = int(math.floor(math.log1p(-u) / math.log1p(-p)))
         return max(w.k_lo, min(w.k_hi, 4 + g))
     return uniform_int(w.query_seed, 5, i, w.k_lo, w.k_hi)
@@ -357,7 +373,9 @@ def queries(name: str, count: int | None = None, start: int = 0) -> list[Query]:
     from concurrent.futures import ThreadPoolExecutor
 
     def one(i):
-        return walk_query(g, w.query_seed, i, drawn_size(w, i), dense=(i % 2 == 1), max_bound=w.max_bound)
+        k = drawn_size(w, i)
+        rare = w.min_label if (w.min_label and k >= w.rare_from_k) else 0
+        return walk_query(g, w.query_seed, i, k, dense=(i % 2 == 1), max_bound=w.max_bound, min_label=rare)
 
     with ThreadPoolExecutor(max_workers=_threads()) as ex:
         return list(ex.map(one, idx))

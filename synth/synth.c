@@ -523,27 +523,34 @@ double synth_tree_hom_bound(void *p, int32_t k, const int32_t *qvlab, const int3
  * vertex (one occurrence, so every query has at least one embedding).
  */
 int32_t synth_walk_query(void *p, const int32_t *vlab, uint64_t seed, int64_t qindex, int32_t k, int32_t dense,
-                         double max_bound, int32_t nthreads, int32_t max_attempts,
+                         double max_bound, int32_t nthreads, int32_t max_attempts, int32_t min_label,
                          int32_t *qvlab, int32_t *qsrc, int32_t *qdst, int32_t *qelab, int32_t *qverts,
-                         double *bound_out) {
+                         double *bound_out, int32_t *attempts_out) {
     adj_t *g = (adj_t *)p;
     
     if (k < 1 || k > 32) return -1;
+    if (attempts_out) *attempts_out = 0;
     int32_t maxe = k * (k - 1) / 2;
     uint8_t *has = (uint8_t *)calloc((size_t)k * k, 1);
     if (max_attempts <= 0 || max_attempts > 100000) max_attempts = 100000;
     for (int attempt = 0; attempt < max_attempts; ++attempt) {
         uint64_t ctr = (uint64_t)qindex * 100000 + (uint64_t)attempt;
         int32_t start = (int32_t)draw_below(seed, ST_QSTART, ctr, (uint64_t)g->n);
+        if (attempts_out) *attempts_out = attempt + 1;
         if (g->start[start + 1] == g->start[start] && k > 1) continue;
+        /* rare-label walks visit only vertices labelled min_label or above */
+        if (g->vlab[start] < min_label) continue;
         memset(has, 0, (size_t)k * k);
         int32_t nv = 1, ne = 0, cur = start, curq = 0;
         qverts[0] = start;
-        int64_t maxsteps = 64 * (int64_t)k;
+        int64_t maxsteps = (min_label > 0 ? 256 : 64) * (int64_t)k;
         for (int64_t st = 0; st < maxsteps && nv < k; ++st) {
             int64_t deg = g->start[cur + 1] - g->start[cur];
-            int64_t pick = (int64_t)draw_below(seed, ST_QWALK, ctr * 1024 + (uint64_t)st, (uint64_t)deg);
+            /* counter space per attempt: 1024 steps (4096 for rare-label walks) */
+            const uint64_t wctr = min_label > 0 ? ctr * 8192 + (uint64_t)st : ctr * 1024 + (uint64_t)st;
+            int64_t pick = (int64_t)draw_below(seed, ST_QWALK, wctr, (uint64_t)deg);
             int32_t nb = g->nbr[g->start[cur] + pick];
+            if (g->vlab[nb] < min_label) continue;    /* a step to a frequent label is not taken */
             int32_t nbq = -1;
             for (int32_t i = 0; i < nv; ++i) if (qverts[i] == nb) { nbq = i; break; }
             if (nbq < 0) { nbq = nv; qverts[nv++] = nb; }

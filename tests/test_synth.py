@@ -57,3 +57,31 @@ def test_walk_query_small_graph():
             assert og.edge_label(int(occ[a]), int(occ[b])) == l
         c = oracle.count(og, q)[0]
         assert 1 <= c <= q.bound
+
+
+def test_rare_label_walks_visit_only_rare_labels():
+    """Rare-label walks (the batched and served workloads' queries of 8 or
+    more vertices) start at and step to vertices labelled min_label or above
+    only; the query is still an occurrence in G with its labels."""
+    s, d = synth.rmat(9, 11, 16000)
+    g = synth.make_graph(synth.labels_zipf(9, 1, 2048, 16), s, d, synth.labels_uniform(9, 2, 16000, 3), 3)
+    og = oracle.OracleGraph.from_synth(g)
+    for i in range(8):
+        q = synth.walk_query(g, 78, i, 8, dense=bool(i % 2), max_bound=1e6, min_label=4)
+        occ = q.occurrence
+        assert len(set(occ.tolist())) == 8 and q.attempts >= 1
+        assert (g.vlab[occ] >= 4).all() and (q.vlab >= 4).all()
+        for a, b, l in zip(q.src, q.dst, q.elab):
+            assert og.edge_label(int(occ[a]), int(occ[b])) == l
+        c = oracle.count(og, q)[0]
+        assert 1 <= c <= q.bound <= 1e6
+
+
+def test_batched_and_served_sizes_span_4_to_16():
+    for name in ("batched", "served"):
+        w = synth.WORKLOADS[name]
+        ks = [synth.drawn_size(w, i) for i in range(2000)]
+        assert min(ks) == 4 and max(ks) == 16
+    w = synth.WORKLOADS["served"]
+    ks = [synth.drawn_size(w, i) for i in range(20000)]
+    assert 7.0 < sum(ks) / len(ks) < 8.2          # geometric with mean 8, clipped at 16
