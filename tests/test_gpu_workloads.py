@@ -1,16 +1,20 @@
-"""The medium and batched configurations at full size, in the launch
+"""The medium, batched and served configurations at full size, in the launch
 configurations the benchmark times.
 
 - medium: R-MAT 2^20 vertices / 16M edges, 64 Zipf vertex labels, 8 edge
   labels, 100 walk queries of 6..12 vertices, one at a time on the plain path.
-- batched: the same graph, 4,096 walk queries of 4..7 vertices as one
-  prepared batch replayed from its captured CUDA graph.
+  Every query's count and full-set fingerprint equal the oracle's, computed
+  once on the CPU into tests/golden/medium_counts.json.
+- batched: the same graph, 4,096 walk queries of 4..16 vertices (rare-label
+  walks from 8 vertices) as one prepared batch replayed from its captured
+  CUDA graph: every count equals the plain path's, and a seeded 256-query
+  sample equals the oracle (counts and full-set fingerprints).
+- served: the 2^22 graph; the first 256 arrivals through a continuous-
+  batching server equal the plain path, a 32-query sample the oracle.
+"""
+import json
+import os
 
-Parity where the oracle finishes in seconds: exact counts and the
-order-independent fingerprints of the whole embedding sets on the oracle
-sample (medium) and on a seeded 256-query sample (batched).  Every other
-query is checked by properties: the admission bound, the definition on its
-first materialised rows, and (batched) equality with the plain path."""
 import numpy as np
 import pytest
 
@@ -67,26 +71,54 @@ def oracle_sample(qs, n=8, max_bound=2e7):
     return [i for i, q in enumerate(qs) if q.bound <= max_bound][:n]
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+FP_CHUNK = 1 << 22
+
+
+def golden_counts(workload):
+    """Per-query oracle counts and fingerprints written by
+    tests/golden/make_counts.py (CPU oracle only)."""
+    with open(os.path.join(GOLDEN, f"{workload}_counts.json")) as f:
+        rec = json.load(f)
+    return {q["index"]: q for q in rec["queries"]}
+
+
+def result_fingerprint(r, k):
+    """The oracle's order-independent fingerprint of a whole result: rows are
+    copied device to device, then fingerprinted on the host chunk by chunk
+    (the fingerprint's sum and xor combine over chunks)."""
+    import torch
+    c = r.count
+    buf = torch.empty((max(c, 1), k), dtype=torch.int32, device="cuda")
+    rows, _ = r.copy_to(buf.data_ptr(), c)
+    s = x = 0
+    for a in range(0, rows, FP_CHUNK):
+        n, s1, x1 = oracle.fingerprint(buf[a:a + FP_CHUNK].cpu().numpy())
+        s = (s + s1) % (1 << 64)
+        x ^= x1
+    first = buf[:min(rows, ROW_SAMPLE)].cpu().numpy()
+    del buf
+    return rows, s, x, first
+
+
 def test_medium_plain_path_full_size(pkg, medium):
+    """Every one of the 100 queries: exact count and full-set fingerprint
+    equal to the oracle's (tests/golden/medium_counts.json), and the first
+    rows satisfy the definition."""
     g, G, O, keys, labs = medium
     assert g.n == 1 << 20 and g.m == 16_000_000
     qs = synth.queries("medium")
-    sample = set(oracle_sample(qs))
-    assert len(sample) == 8
+    want = golden_counts("medium")
+    assert sorted(want) == list(range(len(qs)))
     for i, q in enumerate(qs):
+        assert want[i]["k"] == q.k and want[i]["edges"] == q.qm
         r = G.query(q)
         c = r.count
-        assert c <= q.bound * (1 + 1e-9) + 1
-        if i in sample:
-            want, fp = oracle.count(O, q)
-            assert c == want, i
-            rows = r.rows()
-            assert rows.shape[0] == c
-            assert oracle.fingerprint(rows) == (want, fp[1], fp[2]), i
-        else:
-            rows = r.rows(max_rows=ROW_SAMPLE)
-            assert rows.shape[0] == min(c, ROW_SAMPLE)
-            check_rows(g, q, rows, keys, labs)
+        assert c == want[i]["count"], i
+        rows, s, x, first = result_fingerprint(r, q.k)
+        assert rows == c
+        assert (c, s, x) == tuple(int(v) for v in want[i]["fingerprint"]), i
+        check_rows(g, q, first, keys, labs)
         r.close()
 
 
