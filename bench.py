@@ -215,18 +215,20 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         return total
 
     tuned = {}
+    knobs = {}
     if batched:
-        spi, rows, ms = pkg.batch_autotune(G, mine[:512], stream=stream, mem_budget=budget)
-        tuned = {"seeds_per_item": spi, "item_rows": rows, "calibration_ms": ms,
-                 "calibration_queries": min(512, len(mine))}
+        best = pkg.batch_autotune_full(G, mine[:512], stream=stream, mem_budget=budget)
+        knobs = {k: best[k] for k in ("seeds_per_item", "item_rows", "isect", "rows_per_thread", "block_threads")}
+        tuned = dict(knobs, calibration_ms=best["ms"], calibration_runs=best["trials"],
+                     calibration_queries=min(512, len(mine)),
+                     isect_name=["binary search", "merge", "bitmap"][best["isect"]])
 
     prepared = None
     if batched:
         # planned once, replayed from a captured CUDA graph: every step reruns
         # the filter and the whole join on the device
-        prepared = pkg.PreparedBatch(G, mine, stream=stream, row_cap=row_cap, mem_budget=budget,
-                                     seeds_per_item=tuned["seeds_per_item"], item_rows=tuned["item_rows"],
-                                     counters=True)
+        prepared = pkg.PreparedBatch(G, mine, stream=stream, row_cap=row_cap, mem_budget=budget, counters=True,
+                                     **knobs)
 
     def batch_step(stats_list=None):
         st = pkg.c_stats() if stats_list is not None else None
@@ -293,13 +295,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     filter_bytes = sum(s.filter_bytes for s in stats)
     kernels = sum(s.kernels for s in stats)
     host_driven = sum(s.host_driven for s in stats)
+    join_bytes_lw = sum(s.join_bytes_listwise for s in stats)
     allv = combine([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
-                    float(join_launches), filter_ms, float(filter_bytes), float(kernels)], world, device="cuda")
+                    float(join_launches), filter_ms, float(filter_bytes), float(kernels), float(join_bytes_lw)],
+                   world, device="cuda")
     t_max_ms = float(allv[:, 0].max())
     tot_emb = float(allv[:, 1].sum())
     tot_q = float(allv[:, 2].sum())
 
     # ---- end to end through the public API with host buffers
+    # Every query is submitted with host arrays (uploaded by the library) and
+    # all its rows are copied to pinned host memory.  The copy of query i runs
+    # on a copy stream while query i + 1 computes; a result is released only
+    # after its copy has completed (the query stream waits for the copy).
     e2e = None
     if args.e2e_steps > 0:
         import torch as _t
@@ -309,7 +317,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
             counts.append((r.count, cols(q)))
             r.close()
         max_bytes = max([min(c, row_cap or c) * k * 4 for c, k in counts] + [4])
-        host = _t.empty(max_bytes // 4 + 1, dtype=_t.int32, pin_memory=True)
+        hosts = [_t.empty(max_bytes // 4 + 1, dtype=_t.int32, pin_memory=True) for _ in range(2)]
+        copy_stream = _t.cuda.Stream()
         h2d = sum(q.vlab.nbytes + q.src.nbytes + q.dst.nbytes + q.elab.nbytes for q in mine)
         d2h = 0
         emb = 0
@@ -317,28 +326,42 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             if batched:
-                res = G.batch(mine, stream=stream, row_cap=row_cap, seeds_per_item=tuned.get("seeds_per_item", 0),
-                              item_rows=tuned.get("item_rows", 0))
-                for q, r in zip(mine, res):
+                res = G.batch(mine, stream=stream, row_cap=row_cap, **knobs)
+                done = []
+                for j, (q, r) in enumerate(zip(mine, res)):
                     c = r.count
-                    rows, _capped = r.copy_to(host.data_ptr(), c)
+                    rows, _capped = r.copy_to_async(hosts[j % 2].data_ptr(), c, stream=copy_stream)
                     d2h += rows * cols(q) * 4 + 8
                     emb += c
+                    done.append(r)
+                copy_stream.synchronize()
+                for r in done:
                     r.close()
                 continue
-            for q in mine:
+            prev = None
+            for j, q in enumerate(mine):
                 r = G.query(q, stream=stream, row_cap=row_cap)
+                if prev is not None:                 # released after its copy, ordered on the query stream
+                    stream.wait_event(prev[1])
+                    prev[0].close()
                 c = r.count
-                rows, _capped = r.copy_to(host.data_ptr(), c)
+                rows, _capped = r.copy_to_async(hosts[j % 2].data_ptr(), c, stream=copy_stream)
+                ev = _t.cuda.Event()
+                ev.record(copy_stream)
                 d2h += rows * cols(q) * 4 + 8
                 emb += c
-                r.close()
+                prev = (r, ev)
+            copy_stream.synchronize()
+            if prev is not None:
+                prev[0].close()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e = {"value": emb / el if el > 0 else None, "unit": unit,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // args.e2e_steps),
                "steps": args.e2e_steps, "ms_per_step": el * 1e3 / args.e2e_steps,
-               "queries_per_s": len(mine) * args.e2e_steps / el if el > 0 else None}
+               "queries_per_s": len(mine) * args.e2e_steps / el if el > 0 else None,
+               "d2h_gbs": d2h / el / 1e9 if el > 0 else None,
+               "overlap": "each query's rows copied to pinned host memory on a second stream while the next query runs"}
 
     if rank != 0:
         return None
@@ -354,12 +377,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                 "frac": (achieved / (hbm_peak or 6800.0)) if achieved else None,
                 "traffic": traffic, "traffic_source": traffic_src,
                 "alg_bytes_per_launch": jb / jl if jl else None, "launches": int(jl),
+                "whole_list_model": {
+                    "bytes_per_launch": float(allv[:, 9].sum()) / jl if jl else None,
+                    "achieved": (float(allv[:, 9].sum()) / jl) / ((jms / jl) * 1e-3) / 1e9 if jl and jms else None,
+                    "note": "each linking list N(v,l) counted whole, 8 B to locate it, one 4 B bitmap probe per "
+                            "candidate slot; the roofline above counts label sub-lists and 16 B per list"},
                 "avg_launch_us": jms / jl * 1e3 if jl else None,
                 "share_of_device_time": jms / (t_max_ms * world) if t_max_ms else None}
     fb, fms = float(allv[:, 7].sum()), float(allv[:, 6].sum())
     cfg = {"workload": args.workload, "graph": w.graph.kind + f" n={w.graph.n} m={w.graph.m}",
            "query_subset": args.queries or "all", "vertex_labels": w.graph.n_vlabels, "edge_labels": w.graph.n_elabels,
            "queries": w.n_queries, "k_range": [w.k_lo, w.k_hi], "query_admission_bound": w.max_bound,
+           "walk_attempts": int(sum(q.attempts for q in queries)),
+           "rare_label_walks_from_k": w.rare_from_k or None, "min_label": w.min_label or None,
            "row_cap": w.row_cap, "l2": "flushed between timed steps (512 MB write)",
            "materialised": True, "parallelism": f"queries sharded over {world} GPU(s)",
            "launch": ("one prepared batch per step, replayed from a captured CUDA graph (filter + batch kernel)"
@@ -443,13 +473,14 @@ def run_served(args) -> dict:
     G = pkg.Graph.from_synth(g)
     budget = int((args.budget_gb or 40) * (1 << 30))            # the served configuration's 40 GB budget
 
-    spi, rows, _ = pkg.batch_autotune(G, queries[:64], mem_budget=budget // max(1, args.served_slots))
+    best = pkg.batch_autotune_full(G, queries[:256], mem_budget=8 << 30)
+    knobs = {k: best[k] for k in ("seeds_per_item", "item_rows", "isect", "rows_per_thread", "block_threads")}
 
     def make(kind):
         if kind == "plain":
             return pkg.Server(G, mem_budget=budget, n_streams=1, max_batch=1)
-        return pkg.Server(G, mem_budget=budget, n_streams=args.served_slots, max_batch=0, seeds_per_item=spi,
-                          item_rows=rows, min_batch=args.served_min_batch)
+        return pkg.Server(G, mem_budget=budget, n_streams=args.served_slots, max_batch=0,
+                          min_batch=args.served_min_batch, **knobs)
 
     def closed_loop(kind):
         S = make(kind)
@@ -500,10 +531,15 @@ def run_served(args) -> dict:
         return {"rate": rate, "achieved_qps": nq / el, "embeddings_per_s": emb[0] / el,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
+    sampler = ClockSampler(0)
+    sampler.start()
+    t_sweep = time.perf_counter()
     cap_plain, emb_plain = closed_loop("plain")
     cap_batch, emb_batch = closed_loop("batched")
-    rates = [f * cap_plain for f in (0.5, 1.0, 1.25, 1.5, 2.0, 3.0, 4.0)]
+    rates = [f * cap_plain for f in (0.5, 1.0, 1.25, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0)]
     sweep = {"plain": [open_loop("plain", r) for r in rates], "batched": [open_loop("batched", r) for r in rates]}
+    sweep_s = time.perf_counter() - t_sweep
+    clocks = sampler.stop()
 
     def at_p99(rows, lim):
         return max([x["achieved_qps"] for x in rows if x["p99_ms"] <= lim] or [0.0])
@@ -518,12 +554,17 @@ def run_served(args) -> dict:
             "config": {"workload": "served", "graph": f"rmat n={w.graph.n} m={w.graph.m}",
                        "queries": f"first {nq} of the {w.n_queries}-query stream", "k_range": [w.k_lo, w.k_hi],
                        "query_admission_bound": w.max_bound, "slots": args.served_slots,
-                       "autotuned_seeds_per_item": spi, "autotuned_item_rows": rows, "min_batch": args.served_min_batch or 16,
+                       "rare_label_walks_from_k": w.rare_from_k or None, "min_label": w.min_label or None,
+                       "walk_attempts": int(sum(q.attempts for q in queries)),
+                       "autotuned": knobs, "min_batch": args.served_min_batch or 16,
+                       "admission": "per-request estimate of the first intermediate table x 16, at least 4 GiB per "
+                                    "batch, against the memory budget",
                        "memory_budget_bytes": budget},
             "closed_loop": {"plain": {"queries_per_s": cap_plain, "embeddings_per_s": emb_plain},
                             "batched": {"queries_per_s": cap_batch, "embeddings_per_s": emb_batch}},
             "latency_slo_ms": slo, "latency_slo": "p99 of the plain path offered its closed-loop capacity",
-            "queries_per_s_at_slo": best, "queries_per_s_at_p99_ms": table, "sweep": sweep, "mode": "served"}
+            "queries_per_s_at_slo": best, "queries_per_s_at_p99_ms": table, "sweep": sweep, "mode": "served",
+            "clocks": clocks, "wall_s": sweep_s}
 
 
 # --------------------------------------------------------------- reference arm
@@ -582,7 +623,7 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"],
                     help="plain: one query at a time; batched: one gsi_batch_run per step (auto: by workload)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
-    ap.add_argument("--served-queries", type=int, default=2000, help="prefix of the served arrival stream")
+    ap.add_argument("--served-queries", type=int, default=20000, help="prefix of the served arrival stream")
     ap.add_argument("--served-slots", type=int, default=2)
     ap.add_argument("--served-min-batch", type=int, default=0,
                     help="batching server: fewer pending requests run one by one on the plain path (0 = library default)")

@@ -120,7 +120,12 @@ typedef struct {
     double filter_ms, join_ms, other_ms;
     uint64_t filter_launches, join_launches, other_launches;
     uint64_t filter_bytes;   /* algorithmic bytes of the filter */
-    uint64_t join_bytes;     /* algorithmic bytes of the join steps */
+    uint64_t join_bytes;     /* algorithmic bytes of the join steps: per row
+                                the row, 16 bytes per linking list (its offset
+                                pair and label sub-range), the label
+                                sub-lists (the shortest once per candidate
+                                slot, with the bitmap word), and 4(t+1) per
+                                survivor written */
     uint64_t join_items;     /* candidate slots: sum over rows of the length
                                 of the row's shortest linking list restricted
                                 to the new vertex's label (a bound at most
@@ -134,6 +139,11 @@ typedef struct {
     uint64_t cand[GSI_MAX_QUERY_VERTICES];   /* |C(u)| per query vertex */
     int32_t order[GSI_MAX_QUERY_VERTICES];   /* join order (query vertex ids) */
     int32_t k;
+    uint64_t join_bytes_listwise;   /* join_bytes under the whole-list model:
+                                       each linking list N(v,l) read whole,
+                                       8 bytes to locate it, one 4-byte bitmap
+                                       probe per candidate slot (device-driven
+                                       and batched paths) */
 } gsi_stats;
 
 /* Query semantics.  GSI_ISOMORPHISM: Defs. 2-3 (injective maps).
@@ -179,18 +189,33 @@ gsi_status gsi_query_run(gsi_graph *g, const int32_t *qvlab, int32_t k, const in
                          const int32_t *qdst, const int32_t *qelab, int32_t qm, const gsi_query_opts *opts,
                          gsi_result **out);
 
-/* Exact number of embeddings (also beyond the row cap). */
+/* Exact number of embeddings (also beyond the row cap): the size of the set
+ * of subgraph isomorphisms of Def. 3, i.e. the rows of Alg. 2's final table. */
 gsi_status gsi_result_count(const gsi_result *r, uint64_t *count);
 /* Number of query vertices k (columns of each row). */
 gsi_status gsi_result_columns(const gsi_result *r, int32_t *k);
 /*
  * Copy up to max_rows materialised embeddings into dst (host or device
  * memory; the library detects which), row-major int32[rows][k], column j =
- * query vertex j.  Row order is unspecified.  *rows receives the number
- * copied.  Returns GSI_ECAPPED when fewer rows were materialised than the
- * count (row cap or count-only), GSI_OK otherwise.
+ * query vertex j: Alg. 2's final table with its columns in query-vertex
+ * order (each row is one match f of Def. 3, f(u_j) in column j).  Row order
+ * is unspecified.  *rows receives the number copied.  Returns GSI_ECAPPED
+ * when fewer rows were materialised than the count (row cap or count-only),
+ * GSI_OK otherwise.  Returns when the copy is complete.
  */
 gsi_status gsi_result_copy(const gsi_result *r, int32_t *dst, uint64_t max_rows, uint64_t *rows);
+/*
+ * gsi_result_copy enqueued on `stream` (cudaStream_t, null = the legacy
+ * default stream) instead of completed: *rows and the status are known at
+ * once, the bytes land when the stream reaches the copy.  dst should be
+ * pinned host memory (or device memory) for the copy to run asynchronously.
+ * The result must stay alive until the copy has completed: synchronise the
+ * stream, or make the stream that produced the result wait for it, before
+ * gsi_result_destroy.  Use: copying one query's rows to the host while the
+ * next query runs on another stream.
+ */
+gsi_status gsi_result_copy_async(const gsi_result *r, int32_t *dst, uint64_t max_rows, uint64_t *rows,
+                                 void *stream);
 /* Releases the result's device memory stream-ordered on the stream it was
    produced on: destroy results before destroying that stream. */
 void gsi_result_destroy(gsi_result *r);
@@ -278,7 +303,24 @@ typedef struct {
                                 rows than this after a step keeps this many and
                                 queues the rest, in pieces of this many rows,
                                 for other CTAs; 0 = 1024, < 0 = never split */
+    int32_t isect;           /* how short rows of multi-edge steps intersect
+                                their candidates with the other linking lists:
+                                GSI_ISECT_BSEARCH (0, default),
+                                GSI_ISECT_MERGE, GSI_ISECT_BITMAP */
+    int32_t rows_per_thread; /* rows one thread joins per batch of the row
+                                pass: 1 or 2 (0 = 2) */
+    int32_t block_threads;   /* threads per CTA of the batch kernel: 128 or
+                                256 (0 = 256) */
 } gsi_batch_opts;
+
+/* Intersection strategies (gsi_batch_opts.isect); all give the same set.
+ * BSEARCH searches each candidate in each other linking list; MERGE walks
+ * each other list beside the candidates (both sorted); BITMAP searches each
+ * element of each other list among the candidates and ANDs the resulting
+ * candidate-position masks. */
+#define GSI_ISECT_BSEARCH 0
+#define GSI_ISECT_MERGE 1
+#define GSI_ISECT_BITMAP 2
 
 /*
  * Run nq queries together in one persistent launch (no counterpart in the
@@ -302,10 +344,21 @@ gsi_status gsi_batch_run(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, con
  * given calibration batch once per candidate pair (seeds_per_item in
  * {32, 64, 128}) x (item_rows in {512, 1024, 2048}), each twice, and returns
  * the fastest pair in *best_seeds_per_item / *best_item_rows with its time in
- * *best_ms (all optional).
+ * *best_ms (all optional).  gsi_batch_autotune_full tunes every knob.
  */
 gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
                               int32_t *best_seeds_per_item, int32_t *best_item_rows, double *best_ms);
+/*
+ * The full autotuner: coordinate descent over seeds_per_item {32, 64, 128},
+ * item_rows {512, 1024, 2048}, isect {BSEARCH, MERGE, BITMAP} and the block
+ * shape (block_threads, rows_per_thread) in {256, 128} x {2, 1}, one knob at
+ * a time from the defaults, each candidate timed twice on the calibration
+ * batch (wall time of gsi_batch_run).  *best receives opts with the chosen
+ * knobs (stream, budget and the rest copied from opts), *best_ms the time of
+ * the chosen setting; trials (optional) the number of batch runs made.
+ */
+gsi_status gsi_batch_autotune_full(gsi_graph *g, const gsi_query_desc *qs, int32_t nq, const gsi_batch_opts *opts,
+                                   gsi_batch_opts *best, double *best_ms, int32_t *trials);
 
 /*
  * Prepared batches (no counterpart in the paper): the batch of gsi_batch_run
@@ -334,14 +387,15 @@ void gsi_batch_destroy(gsi_batch *b);
 
 /* ---------------------------------------------------------------- served */
 typedef struct {
-    uint64_t mem_budget;     /* bytes for intermediate tables, split evenly over
-                                the slots; 0 = half of the device's free
-                                memory at creation */
+    uint64_t mem_budget;     /* device memory for the intermediate tables of
+                                the requests running at once (admission
+                                budget, see gsi_server_create); 0 = half of
+                                the device's free memory at creation */
     int32_t n_streams;       /* slots: worker threads, each with its own stream
                                 (0 = 2) */
     uint64_t row_cap;        /* per query */
     int32_t count_only;
-    int32_t max_batch;       /* requests a slot takes at once (0 = all pending);
+    int32_t max_batch;       /* requests a slot takes at once (0 = 2048);
                                 1 = one query at a time on the plain path */
     int32_t seeds_per_item;  /* batch work-item size (0 = 32); see
                                 gsi_batch_autotune */
@@ -350,20 +404,39 @@ typedef struct {
                                 time on the plain path (every step on all SMs:
                                 lower latency than a batch too small to fill
                                 the GPU); 0 = 16 */
+    int32_t isect;           /* batches: see gsi_batch_opts */
+    int32_t rows_per_thread;
+    int32_t block_threads;
 } gsi_server_opts;
 
 /*
  * A serving loop over a resident graph (continuous batching, no counterpart
- * in the paper): each slot takes every pending request, up to max_batch, as
- * one batch and runs it on its own stream within its memory share, so
- * requests arriving while other batches are on the GPU join the next free
- * slot and slots overlap on the device.  With fewer than min_batch requests
- * pending a slot runs them one at a time on the plain path.  Creation
- * reserves each slot's batch workspace (its share of mem_budget) so that no
- * request waits for it; if that fails, batches reserve their memory as they
- * run.  The graph must outlive the server.
+ * in the paper).  Each request carries an estimate of its intermediate-table
+ * memory (gsi_server_estimate).  A slot takes pending requests in arrival
+ * order, up to max_batch, while the batch's reservation -- the sum over its
+ * requests of 16 times the estimate or 1 MiB, whichever is larger, and at
+ * least 4 GiB in all -- fits what the running batches leave
+ * of mem_budget, runs them as one batch on its own stream in a work area of
+ * that size (taken from the device's stream-ordered pool), and returns the
+ * reservation when the results are out.  Requests arriving while others are
+ * on the GPU are admitted as soon as a slot and memory free up, and batches
+ * of different slots overlap on the device.  A request too large for the
+ * budget on its own runs alone.  With fewer than min_batch requests taken a
+ * slot runs them one at a time on the plain path, within the same
+ * reservation.  Creation counts the graph's directed edges per (vertex label,
+ * vertex label, edge label) on the device for the estimates.  The graph must
+ * outlive the server.
  */
 gsi_status gsi_server_create(gsi_graph *g, const gsi_server_opts *opts, gsi_server **out);
+/*
+ * The admission estimate of a query, in bytes: the fewest directed data edges
+ * matching one of its query edges by (label of one end, label of the other,
+ * edge label), times 8 -- the Alg. 4 preallocation bound of a first join
+ * step along that edge before filtering, with two int32 columns per row.
+ * Host only (uses the counts made at creation).  GSI_EINVAL for an invalid
+ * query.
+ */
+gsi_status gsi_server_estimate(gsi_server *s, const gsi_query_desc *q, uint64_t *bytes);
 /* Enqueue a query (copied).  *ticket identifies it in gsi_server_poll. */
 gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, uint64_t *ticket);
 /*

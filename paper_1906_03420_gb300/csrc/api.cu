@@ -227,6 +227,33 @@ gsi_status gsi_result_copy(const gsi_result *r, int32_t *dst, uint64_t max_rows,
     return r->materialised < r->count ? GSI_ECAPPED : GSI_OK;
 }
 
+gsi_status gsi_result_copy_async(const gsi_result *r, int32_t *dst, uint64_t max_rows, uint64_t *rows,
+                                 void *stream) {
+    if (!r || (!dst && max_rows > 0)) {
+        set_error("gsi_result_copy_async: null argument");
+        return GSI_EINVAL;
+    }
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != r->device) cudaSetDevice(r->device);
+    uint64_t done = 0;
+    for (const auto &c : r->chunks) {
+        if (done >= max_rows) break;
+        uint64_t take = std::min<uint64_t>(c.nrows, max_rows - done);
+        cudaError_t e = cudaMemcpyAsync(dst + done * (uint64_t)r->k, c.rows, take * (uint64_t)r->k * 4,
+                                        cudaMemcpyDefault, (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            set_error(std::string("gsi_result_copy_async: ") + cudaGetErrorString(e));
+            if (cur >= 0 && cur != r->device) cudaSetDevice(cur);
+            return GSI_ECUDA;
+        }
+        done += take;
+    }
+    if (cur >= 0 && cur != r->device) cudaSetDevice(cur);
+    if (rows) *rows = done;
+    return r->materialised < r->count ? GSI_ECAPPED : GSI_OK;
+}
+
 void gsi_result_destroy(gsi_result *r) { delete r; }
 
 gsi_status gsi_query_signatures(const int32_t *qvlab, int32_t k, const int32_t *qsrc, const int32_t *qdst,

@@ -31,9 +31,7 @@
 namespace gsi {
 namespace {
 
-constexpr int BNT = JOIN_NT;
 constexpr int BVT = JOIN_VT;
-constexpr int BNV = BNT * BVT;
 constexpr uint64_t SPILL_SLOTS = 1ull << 18;                  // spill queue capacity (units)
 constexpr unsigned long long WAIT_SPIN_LIMIT = 1ull << 26;    // x ~100 ns sleeps: several seconds
 constexpr long long UNIT_DONE = -(1ll << 62);
@@ -137,7 +135,11 @@ __device__ long long next_unit(const BatchArgs &b) {
     }
 }
 
-__global__ void __launch_bounds__(BNT, 4) k_batch(const __grid_constant__ BatchArgs b) {
+// One instance per block shape: NT threads per CTA, RPT rows per thread in
+// the row pass (the batched autotuner picks one).
+template <int NT, int RPT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_batch(const __grid_constant__ BatchArgs b) {
+    constexpr int BNT = NT, BNV = NT * BVT;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long wt[BNT / 32];
     __shared__ long long unit_s;
@@ -231,14 +233,17 @@ __global__ void __launch_bounds__(BNT, 4) k_batch(const __grid_constant__ BatchA
             }
             __syncthreads();
             // short rows joined inline, long rows set aside
-            unsigned long long abytes = 0, items = 0;
-            row_pass<BNT>(a, M, R, 0, BNT * ROW_RPT, out, cap, &cnt_s, lt, &rfail_s, smem, &abytes, &items);
+            unsigned long long abytes = 0, items = 0, lbytes = 0;
+            row_pass<BNT, true, RPT>(a, M, R, 0, (uint64_t)BNT * RPT, out, cap, &cnt_s, lt, &rfail_s, smem, &abytes,
+                                     &items, &lbytes);
             if (a.stats) {                       // one add per step of a unit
                 abytes = block_sum<BNT, unsigned long long>(abytes, wt);
                 items = block_sum<BNT, unsigned long long>(items, wt);
+                lbytes = block_sum<BNT, unsigned long long>(lbytes, wt);
                 if (threadIdx.x == 0) {
                     if (abytes) atomicAdd(a.stats, abytes);
                     if (items) atomicAdd(a.stats + 1, items);
+                    if (lbytes) atomicAdd(a.stats + 2, lbytes);
                 }
             }
             __syncthreads();
@@ -277,8 +282,10 @@ __global__ void __launch_bounds__(BNT, 4) k_batch(const __grid_constant__ BatchA
             }
             __syncthreads();
             const uint64_t cnt = cnt_s;
-            if (a.stats && threadIdx.x == 0)     // survivors written
+            if (a.stats && threadIdx.x == 0) {   // survivors written (both models)
                 atomicAdd(a.stats, 4ull * (uint64_t)(t + 1) * min(cnt, cap));
+                atomicAdd(a.stats + 2, 4ull * (uint64_t)(t + 1) * min(cnt, cap));
+            }
             if (!last && cnt > cap) { failed = true; break; }
             M = out;
             oreg ^= 1;
@@ -392,6 +399,13 @@ __global__ void __launch_bounds__(256) k_gather(const BatchQuery *__restrict__ q
 }  // namespace
 
 
+// The batch kernel for a block shape (threads per CTA, rows per thread).
+using BatchKernel = void (*)(BatchArgs);
+BatchKernel batch_kernel(int nt, int rpt) {
+    if (nt == 128) return rpt == 1 ? k_batch<128, 1> : k_batch<128, 2>;
+    return rpt == 1 ? k_batch<256, 1> : k_batch<256, 2>;
+}
+
 // ------------------------------------------------------------------- host
 // Sizes the launch, lists the seed units, builds the per-step configurations
 // and reserves the control block (and the work area unless a workspace brings
@@ -402,8 +416,16 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
     L = BatchLaunch();
     const int nq = (int)plans.size();
     L.nq = (size_t)nq;
+    if ((o.block_threads != 0 && o.block_threads != 128 && o.block_threads != 256) ||
+        (o.rows_per_thread != 0 && o.rows_per_thread != 1 && o.rows_per_thread != 2) || o.isect < 0 ||
+        o.isect > ISECT_BITMAP) {
+        set_error("batch: block_threads must be 128 or 256, rows_per_thread 1 or 2, isect a GSI_ISECT_* value");
+        return GSI_EINVAL;
+    }
+    L.nt = o.block_threads ? o.block_threads : 256;
+    L.rpt = o.rows_per_thread ? o.rows_per_thread : 2;
     if (stats) {
-        GSI_CUDA_TRY(cudaMallocAsync(&L.dstats, 16, st));
+        GSI_CUDA_TRY(cudaMallocAsync(&L.dstats, 24, st));
     }
     size_t sm = join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, 1, 1);
     for (int i = 0; i < nq; ++i) {
@@ -411,7 +433,7 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
         if (!p.active) continue;
         for (int t = 1; t < p.k; ++t) {
             sm = std::max(sm, join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, p.steps[t].t, p.steps[t].d));
-            sm = std::max(sm, rows_smem(BNT, p.steps[t].t));
+            sm = std::max(sm, rows_smem(L.nt, p.steps[t].t, L.rpt));
         }
     }
     if (sm > 200 * 1024) {
@@ -422,8 +444,9 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
-    GSI_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BNT, sm));
+    const BatchKernel kern = batch_kernel(L.nt, L.rpt);
+    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.nt, sm));
     if (per_sm < 1) {
         set_error("batch: kernel does not fit on an SM");
         return GSI_EINVAL;
@@ -466,6 +489,7 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
             const int co = (t == p.k - 1) && o.count_only;
             cfg[(size_t)bqs[i].cfg0 + t] =
                 make_join_args(g, p.steps[t], p.bitmaps + (uint64_t)p.order[t] * (uint64_t)g->nwords, co, L.dstats);
+            cfg[(size_t)bqs[i].cfg0 + t].isect = o.isect;
         }
         // word ranges of the seed bitmap holding about seeds_per_item seeds each
         const uint64_t nw = (uint64_t)g->nwords;
@@ -551,7 +575,7 @@ gsi_status batch_enqueue_kernel(BatchLaunch &L, cudaStream_t st) {
     else
         GSI_CUDA_TRY(cudaMemcpyAsync(d_q, L.q_init.data(), L.q_init.size(), cudaMemcpyHostToDevice, st));
     if (L.sq_cap) GSI_CUDA_TRY(cudaMemsetAsync(L.ctl + L.o_ready, 0, sizeof(unsigned) * L.sq_cap, st));
-    if (L.dstats) GSI_CUDA_TRY(cudaMemsetAsync(L.dstats, 0, 16, st));
+    if (L.dstats) GSI_CUDA_TRY(cudaMemsetAsync(L.dstats, 0, 24, st));
     if (L.nitems == 0) return GSI_OK;
     BatchArgs ba;
     ba.cfgs = reinterpret_cast<const JoinArgs *>(L.ctl);
@@ -571,7 +595,7 @@ gsi_status batch_enqueue_kernel(BatchLaunch &L, cudaStream_t st) {
     ba.t_bytes = L.t_bytes;
     ba.split_rows = L.split_rows;
     ba.spin_limit = WAIT_SPIN_LIMIT;
-    k_batch<<<L.grid, BNT, L.sm, st>>>(ba);
+    batch_kernel(L.nt, L.rpt)<<<L.grid, L.nt, L.sm, st>>>(ba);
     GSI_CUDA_TRY(cudaGetLastError());
     return GSI_OK;
 }
@@ -615,10 +639,11 @@ gsi_status batch_collect(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &p
         }
     }
     if (stats) {
-        unsigned long long hb[2] = {0, 0};
-        if (L.dstats && cudaMemcpy(hb, L.dstats, 16, cudaMemcpyDeviceToHost) != cudaSuccess) hb[0] = hb[1] = 0;
+        unsigned long long hb[3] = {0, 0, 0};
+        if (L.dstats && cudaMemcpy(hb, L.dstats, 24, cudaMemcpyDeviceToHost) != cudaSuccess) hb[0] = hb[1] = hb[2] = 0;
         stats->join_bytes += hb[0];
         stats->join_items += hb[1];
+        stats->join_bytes_listwise += hb[2];
         stats->tiles += rctl.units;
     }
     // a wait that ran out leaves units undone: every query goes to the plain path

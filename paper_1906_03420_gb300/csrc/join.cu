@@ -308,15 +308,17 @@ __global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cf
         if (blockIdx.x == 0 && threadIdx.x == 0) st->out_cap = cap;
         __syncthreads();
         // ---- short rows joined inline, long rows set aside (one pass over M)
-        unsigned long long abytes = 0, items = 0;
+        unsigned long long abytes = 0, items = 0, lbytes = 0;
         row_pass<NT>(a, st->M, R, (uint64_t)blockIdx.x * NT * ROW_RPT, (uint64_t)G * NT * ROW_RPT, st->out, cap,
-                     &st->count, lt, &ctl->fail, smem, &abytes, &items);
+                     &st->count, lt, &ctl->fail, smem, &abytes, &items, &lbytes);
         if (a.stats) {                       // one add per CTA and step
             abytes = block_sum<NT, unsigned long long>(abytes, wt);
             items = block_sum<NT, unsigned long long>(items, wt);
+            lbytes = block_sum<NT, unsigned long long>(lbytes, wt);
             if (threadIdx.x == 0) {
                 if (abytes) atomicAdd(a.stats, abytes);
                 if (items) atomicAdd(a.stats + 1, items);
+                if (lbytes) atomicAdd(a.stats + 2, lbytes);
             }
         }
         if (!grid_barrier(ctl, G)) return;
@@ -327,8 +329,11 @@ __global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cf
                                              reinterpret_cast<int64_t *>(st->S + ll.part_off), ll.part_cap, cap,
                                              bsum, wt, &tile_s))
             return;
-        if (a.stats && blockIdx.x == 0 && threadIdx.x == 0)        // survivors written
-            atomicAdd(a.stats, 4ull * (uint64_t)(t + 1) * min((uint64_t)__ldcg(&st->count), cap));
+        if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) {      // survivors written (both models)
+            const unsigned long long wbytes = 4ull * (uint64_t)(t + 1) * min((uint64_t)__ldcg(&st->count), cap);
+            atomicAdd(a.stats, wbytes);
+            atomicAdd(a.stats + 2, wbytes);
+        }
     }
 }
 

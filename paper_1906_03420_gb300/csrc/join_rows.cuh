@@ -81,8 +81,8 @@ constexpr int ROW_SURV = 4;       // survivor-list entries per batch row (more a
 // Dynamic shared memory of the row pass for CTAs of nt threads: nt * ROW_RPT
 // staged rows of t columns, their candidate sub-list starts, then the
 // survivor list (values, local row and candidate position).
-__host__ __device__ constexpr size_t rows_smem(int nt, int t) {
-    return (size_t)nt * ROW_RPT * ((size_t)t * 4 + 4) + (size_t)nt * ROW_RPT * ROW_SURV * 6;
+__host__ __device__ constexpr size_t rows_smem(int nt, int t, int rpt = ROW_RPT) {
+    return (size_t)nt * rpt * ((size_t)t * 4 + 4) + (size_t)nt * rpt * ROW_SURV * 6;
 }
 
 // Bulk prefetch of [p, p + bytes) into L2 (TMA engine, no registers or
@@ -122,6 +122,12 @@ __device__ __forceinline__ uint32_t sublist(const JoinArgs &a, int j, int32_t v,
     if (slot && len <= BOUND_LEN_MASK)
         *slot = (uint64_t)l | ((uint64_t)len << 32) | ((uint64_t)(uint32_t)a.s.t << MEMO_TAG_SHIFT);
     return len;
+}
+
+// Length of the whole linking list N(v, lab[j]) (for the whole-list byte count).
+__device__ __forceinline__ uint32_t whole_len(const JoinArgs &a, int j, int32_t v) {
+    const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+    return __ldg(a.off + seg + 1) - __ldg(a.off + seg);
 }
 
 // Candidates ci[lo + p], p < len <= 32, that are in C(u): bit p of the result.
@@ -164,7 +170,8 @@ __device__ __forceinline__ uint32_t subtract_row(const JoinArgs &a, const int32_
 template <bool DR>
 __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *row, bool valid, int lane,
                                              uint32_t *best_out, uint32_t *lob_out, int *jb_out,
-                                             unsigned long long *abytes, unsigned long long *items) {
+                                             unsigned long long *abytes, unsigned long long *items,
+                                             unsigned long long *lbytes) {
     const int t = a.s.t, d = a.s.d;
     const bool stats = a.stats != nullptr;
     uint32_t mask = 0, best = 0, lob = 0;
@@ -184,6 +191,7 @@ __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *r
         if (valid && best <= (uint32_t)SHORT_MAX) mask = subtract_row(a, row, lob, bm);
         if (valid && stats) {
             *abytes += row_alg_bytes(t, 1, best, best);
+            *lbytes += row_list_bytes(t, 1, whole_len(a, 0, v), best);
             *items += best;
         }
     } else if (valid) {
@@ -215,27 +223,66 @@ __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *r
             }
         }
         if (stats) {
+            uint64_t wsum = 0;
+            for (int j = 0; j < d; ++j) wsum += whole_len(a, j, row[a.s.col[j]]);
             *abytes += row_alg_bytes(t, d, lsum, best);
+            *lbytes += row_list_bytes(t, d, wsum, best);
             *items += best;
         }
         if (best > 0 && best <= (uint32_t)SHORT_MAX) {
             mask = subtract_row(a, row, lob, bitmap_mask(a, lob, best));
             // every other linking list must hold the candidate (Alg. 3)
-            for (uint32_t m = mask; m; m &= m - 1) {
-                const int p = __ffs(m) - 1;
-                const int32_t w = __ldg(a.ci + lob + (uint32_t)p);
-                bool ok = true;
+            if (a.isect == ISECT_BSEARCH) {
+                for (uint32_t m = mask; m; m &= m - 1) {
+                    const int p = __ffs(m) - 1;
+                    const int32_t w = __ldg(a.ci + lob + (uint32_t)p);
+                    bool ok = true;
 #pragma unroll
-                for (int j = 0; j < MEMO_EDGES; ++j)
-                    if (ok && j < d && j != jb) ok = sorted_contains(a.ci + lo4[j], len4[j], w);
-                for (int j = MEMO_EDGES; j < d && ok; ++j) {
-                    if (j == jb) continue;
-                    const uint64_t seg =
-                        (uint64_t)(uint32_t)row[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
-                    ok = ranked_contains(a.ci, a.cl, __ldg(a.off + seg), __ldg(a.off + seg + 1),
-                                         (uint32_t)a.s.ulab, w);
+                    for (int j = 0; j < MEMO_EDGES; ++j)
+                        if (ok && j < d && j != jb) ok = sorted_contains(a.ci + lo4[j], len4[j], w);
+                    if (!ok) mask &= ~(1u << p);
                 }
-                if (!ok) mask &= ~(1u << p);
+            } else {
+#pragma unroll
+                for (int j = 0; j < MEMO_EDGES; ++j) {
+                    if (!mask || j >= d || j == jb) continue;
+                    uint32_t keep = 0;
+                    const uint32_t b0 = lo4[j], b1 = lo4[j] + len4[j];
+                    if (a.isect == ISECT_MERGE) {
+                        // both lists ascend: one pointer into the other list
+                        uint32_t q = b0;
+                        for (uint32_t m = mask; m && q < b1; m &= m - 1) {
+                            const int p = __ffs(m) - 1;
+                            const int32_t w = __ldg(a.ci + lob + (uint32_t)p);
+                            while (q < b1 && __ldg(a.ci + q) < w) ++q;
+                            if (q < b1 && __ldg(a.ci + q) == w) keep |= 1u << p;
+                        }
+                    } else {
+                        // every element of the other list marks its position
+                        // among the candidates
+                        for (uint32_t q = b0; q < b1; ++q) {
+                            const int32_t x = __ldg(a.ci + q);
+                            uint32_t l = 0, h = best;
+                            while (l < h) {
+                                const uint32_t mid = (l + h) >> 1;
+                                if (__ldg(a.ci + lob + mid) < x) l = mid + 1;
+                                else h = mid;
+                            }
+                            if (l < best && __ldg(a.ci + lob + l) == x) keep |= 1u << l;
+                        }
+                    }
+                    mask &= keep;
+                }
+            }
+            for (int j = MEMO_EDGES; j < d && mask; ++j) {      // lists without a memo slot: searched whole
+                if (j == jb) continue;
+                const uint64_t seg = (uint64_t)(uint32_t)row[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+                const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
+                for (uint32_t m = mask; m; m &= m - 1) {
+                    const int p = __ffs(m) - 1;
+                    if (!ranked_contains(a.ci, a.cl, x0, x1, (uint32_t)a.s.ulab, __ldg(a.ci + lob + (uint32_t)p)))
+                        mask &= ~(1u << p);
+                }
             }
         }
     }
@@ -256,7 +303,8 @@ constexpr int ROW_C = 8;          // candidate values of a single-edge group loa
 template <int NT, int RPT>
 __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_t *rowv, int nb, int lane,
                                                  uint32_t *best, uint32_t *lob, uint32_t *mask,
-                                                 unsigned long long *abytes, unsigned long long *items) {
+                                                 unsigned long long *abytes, unsigned long long *items,
+                                                 unsigned long long *lbytes) {
     constexpr int C = ROW_C;
     const int t = a.s.t;
     int32_t v[RPT];
@@ -317,27 +365,32 @@ __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_
         const uint32_t b = __shfl_sync(FULL_MASK, bm[q], leader[q]);
         if (!valid) best[q] = 0;
         mask[q] = (valid && best[q] <= (uint32_t)SHORT_MAX) ? subtract_row(a, rowv + lr * t, lob[q], b) : 0u;
-        if (valid && a.stats) {
-            *abytes += row_alg_bytes(t, 1, best[q], best[q]);
-            *items += best[q];
+        if (a.stats) {                                // whole first-edge list, from the group leader
+            const uint32_t whole = __shfl_sync(FULL_MASK, lead[q] ? whole_len(a, 0, v[q]) : 0u, leader[q]);
+            if (valid) {
+                *abytes += row_alg_bytes(t, 1, best[q], best[q]);
+                *lbytes += row_list_bytes(t, 1, whole, best[q]);
+                *items += best[q];
+            }
         }
     }
 }
 
-// The row pass over rows [first, R) in batches of NT * ROW_RPT rows, batch
+// The row pass over rows [first, R) in batches of NT * RPT rows, batch
 // starts `stride` apart (a grid-strided pass: first = blockIdx.x * NB,
 // stride = gridDim.x * NB; one CTA alone: first = 0, stride = NB).  `a` should
 // live in shared memory.  Survivors go to out (up to cap rows; `count` is
 // exact), long rows to lt.  Bit 1 of *fail is set when the long-row table is
-// full or a bound does not fit its record.  Adds this thread's algorithmic
-// bytes (rows read, lists located and read; survivors are counted by the
-// caller) and candidate slots to *abytes / *items when a.stats is set.
-template <int NT, bool DR = true>
+// full or a bound does not fit its record.  When a.stats is set, adds this
+// thread's algorithmic bytes (rows read, lists located and read; survivors
+// are counted by the caller) to *abytes, the same under the whole-list model
+// to *lbytes, and its candidate slots to *items.
+template <int NT, bool DR = true, int RPT = ROW_RPT>
 __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64_t first, uint64_t stride,
                          int32_t *__restrict__ out, uint64_t cap, unsigned long long *count, const LongTable &lt,
                          unsigned *fail, unsigned char *smem, unsigned long long *abytes,
-                         unsigned long long *items) {
-    constexpr int NW = NT / 32, NB = NT * ROW_RPT, CCAP = NB * ROW_SURV;
+                         unsigned long long *items, unsigned long long *lbytes) {
+    constexpr int NW = NT / 32, NB = NT * RPT, CCAP = NB * ROW_SURV;
     __shared__ uint32_t wt[NW];
     __shared__ unsigned long long base_s, lbase_s;
     const int t = a.s.t, W1 = t + 1;
@@ -358,27 +411,27 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
             prefetch_l2(M + (r0 + stride) * (uint64_t)t, min((uint64_t)NB, R - r0 - stride) * (uint64_t)t * 4);
         for (int e = threadIdx.x; e < nb * t; e += NT) rowv[e] = __ldcg(src + e);
         __syncthreads();
-        // this thread's rows q * NT + tid, q < ROW_RPT (a warp's lanes hold
+        // this thread's rows q * NT + tid, q < RPT (a warp's lanes hold
         // consecutive rows)
-        uint32_t mask[ROW_RPT], best[ROW_RPT], lob[ROW_RPT];
-        int jb[ROW_RPT];
+        uint32_t mask[RPT], best[RPT], lob[RPT];
+        int jb[RPT];
         uint32_t n = 0, nl = 0;
         if (DR && a.s.d == 1) {
-            rows_join_single<NT, ROW_RPT>(a, rowv, nb, lane, best, lob, mask, abytes, items);
+            rows_join_single<NT, RPT>(a, rowv, nb, lane, best, lob, mask, abytes, items, lbytes);
 #pragma unroll
-            for (int q = 0; q < ROW_RPT; ++q) jb[q] = 0;
+            for (int q = 0; q < RPT; ++q) jb[q] = 0;
         } else {
 #pragma unroll
-            for (int q = 0; q < ROW_RPT; ++q) {
+            for (int q = 0; q < RPT; ++q) {
                 const int lr = q * NT + (int)threadIdx.x;
                 const bool valid = lr < nb;
                 mask[q] = row_join<false>(a, rowv + (valid ? lr : 0) * t, valid, lane, &best[q], &lob[q], &jb[q],
-                                          abytes, items);
+                                          abytes, items, lbytes);
                 if (!valid) best[q] = 0;
             }
         }
 #pragma unroll
-        for (int q = 0; q < ROW_RPT; ++q) {
+        for (int q = 0; q < RPT; ++q) {
             n += __popc(mask[q]);
             nl += best[q] > (uint32_t)SHORT_MAX;
         }
@@ -394,7 +447,7 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
         {
             unsigned long long li = lbase_s + (ex >> 16);
 #pragma unroll
-            for (int q = 0; q < ROW_RPT; ++q) {
+            for (int q = 0; q < RPT; ++q) {
                 if (best[q] <= (uint32_t)SHORT_MAX) continue;
                 const int32_t *row = rowv + (q * NT + (int)threadIdx.x) * t;
                 if (li < lt.cap && best[q] <= BOUND_LEN_MASK) {
@@ -423,7 +476,7 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
             // over all threads instead of one serial chain per thread
             uint32_t i = ex & 0xffffu;
 #pragma unroll
-            for (int q = 0; q < ROW_RPT; ++q) {
+            for (int q = 0; q < RPT; ++q) {
                 const int lr = q * NT + (int)threadIdx.x;
                 if (rb == 0 && mask[q]) lobs[lr] = lob[q];
                 for (uint32_t m = mask[q]; m && i < re; m &= m - 1) {

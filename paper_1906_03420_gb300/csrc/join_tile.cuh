@@ -108,6 +108,14 @@ __device__ __forceinline__ unsigned long long row_alg_bytes(int t, int d, uint64
     return 4ull * t + 16ull * d + 4ull * (lsum - best) + 8ull * best;
 }
 
+// The same row under the whole-list model: read the row, locate each linking
+// list with one 8-byte offset pair, read every linking list N(v, l) whole
+// (wsum elements, the merge-intersection bound), and probe the bitmap once
+// per candidate slot.  Survivors add 4(t+1) each, as above.
+__device__ __forceinline__ unsigned long long row_list_bytes(int t, int d, uint64_t wsum, uint32_t best) {
+    return 4ull * t + 8ull * d + 4ull * wsum + 4ull * best;
+}
+
 struct JoinArgs {
     const int32_t *M;
     int64_t R;
@@ -129,7 +137,19 @@ struct JoinArgs {
     // (null: none); table j holds n entries, tagged with the step
     uint64_t *memo;
     int64_t memo_n;
+    int32_t isect;              // intersection strategy of short multi-edge rows (ISECT_*)
+    int32_t pad_;
 };
+
+// How a short row's candidates are intersected with its other linking lists
+// (all give the same set; the batched autotuner picks one per batch):
+//   ISECT_BSEARCH  each candidate is searched in each other label sub-list;
+//   ISECT_MERGE    each other sub-list is walked once beside the candidates
+//                  (both ascending), a two-pointer merge;
+//   ISECT_BITMAP   each element of each other sub-list is searched among the
+//                  candidates, setting a bit per candidate position; the
+//                  masks of all lists are ANDed.
+constexpr int ISECT_BSEARCH = 0, ISECT_MERGE = 1, ISECT_BITMAP = 2;
 
 template <int NT>
 __device__ inline int block_inclusive_max(int v, int *wt) {

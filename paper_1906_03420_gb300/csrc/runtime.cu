@@ -732,10 +732,11 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     }
     if (x.stats && rc == GSI_OK) {
         // algorithmic bytes and candidates counted by the join kernels
-        if (cudaMemcpyAsync(x.h_pinned, x.d_scalars + 1, 16, cudaMemcpyDeviceToHost, x.st) == cudaSuccess &&
+        if (cudaMemcpyAsync(x.h_pinned, x.d_scalars + 1, 24, cudaMemcpyDeviceToHost, x.st) == cudaSuccess &&
             cudaStreamSynchronize(x.st) == cudaSuccess) {
             x.join_bytes = x.h_pinned[0];
             x.join_items = x.h_pinned[1];
+            x.join_bytes_listwise = x.h_pinned[2];
         }
     }
     cudaFreeAsync(x.bitmaps, x.st);
@@ -756,6 +757,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         s->filter_bytes += filter_alg_bytes(g, std::vector<int32_t>(q.vlab, q.vlab + q.k));
         s->join_bytes += x.join_bytes;
         s->join_items += x.join_items;
+        s->join_bytes_listwise += x.join_bytes_listwise;
         s->kernels += x.kernels;
         s->host_driven += (rc == GSI_OK && !empty && x.fell_back) ? 1 : 0;
     }

@@ -91,7 +91,7 @@ struct Exec {
     uint64_t budget = 0, live = 0, peak = 0, tiles = 0;
     uint64_t row_cap = 0;
     int count_only = 0;
-    uint64_t join_bytes = 0, join_items = 0;
+    uint64_t join_bytes = 0, join_items = 0, join_bytes_listwise = 0;
     uint64_t kernels = 0;
     bool fell_back = false;          // the query ran host-driven            // kernels launched (scan = 3, partition, join, filter, seed = 3)
     gsi_result *res = nullptr;
@@ -144,6 +144,7 @@ struct BatchWorkspace {
 // batch_collect reads the outcome back into the plans.
 struct BatchLaunch {
     int grid = 0, nsm = 152;
+    int nt = 256, rpt = 2;                   // block shape of the batch kernel
     size_t sm = 0;
     uint64_t result_bytes = 0, work_bytes = 0, spill_bytes = 0, slices_bytes = 0;
     uint64_t slice = 0, s_bytes = 0, t_bytes = 0, split_rows = 0, sq_cap = 0, rec_cap = 0;

@@ -281,7 +281,146 @@ extern "C" gsi_status gsi_batch_autotune(gsi_graph *g, const gsi_query_desc *qs,
     }
 }
 
+extern "C" gsi_status gsi_batch_autotune_full(gsi_graph *g, const gsi_query_desc *qs, int32_t nq,
+                                              const gsi_batch_opts *opts, gsi_batch_opts *best, double *best_ms,
+                                              int32_t *trials) {
+    if (!g || nq < 1 || !qs || !best) {
+        set_error("gsi_batch_autotune_full: need a graph, at least one query and an output");
+        return GSI_EINVAL;
+    }
+    try {
+        gsi_batch_opts bo;
+        std::memset(&bo, 0, sizeof bo);
+        if (opts) bo = *opts;
+        bo.stats = nullptr;
+        std::vector<BatchPlan> proto((size_t)nq);
+        for (int32_t i = 0; i < nq; ++i)
+            proto[i].status = validate_query(qs[i].vlab, qs[i].k, qs[i].src, qs[i].dst, qs[i].elab, qs[i].qm,
+                                             &proto[i].q);
+        int32_t runs = 0;
+        // best of two runs of the calibration batch with these knobs
+        auto time_of = [&](const gsi_batch_opts &o, double *ms) -> gsi_status {
+            double t_best = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                std::vector<BatchPlan> plans((size_t)nq);
+                for (int32_t i = 0; i < nq; ++i) {
+                    plans[i].status = proto[i].status;
+                    plans[i].q = proto[i].q;
+                }
+                std::vector<gsi_result *> res;
+                std::vector<gsi_status> sts;
+                auto t0 = std::chrono::steady_clock::now();
+                gsi_status rc = batch_execute(g, plans, o, res, sts);
+                if (o.stream) cudaStreamSynchronize((cudaStream_t)o.stream);
+                auto t1 = std::chrono::steady_clock::now();
+                for (gsi_result *r : res) delete r;
+                ++runs;
+                if (rc != GSI_OK) return rc;
+                t_best = std::min(t_best, std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            *ms = t_best;
+            return GSI_OK;
+        };
+        // coordinate descent from the defaults, one knob at a time
+        gsi_batch_opts cur = bo;
+        cur.seeds_per_item = 32;
+        cur.item_rows = 1024;
+        cur.isect = GSI_ISECT_BSEARCH;
+        cur.rows_per_thread = 2;
+        cur.block_threads = 256;
+        double cur_ms = 0;
+        GSI_TRY(time_of(cur, &cur_ms));
+        auto try_knob = [&](auto set, const std::vector<int32_t> &values) -> gsi_status {
+            for (int32_t v : values) {
+                gsi_batch_opts cand = cur;
+                set(cand, v);
+                if (std::memcmp(&cand, &cur, sizeof cand) == 0) continue;
+                double ms = 0;
+                GSI_TRY(time_of(cand, &ms));
+                if (ms < cur_ms) {
+                    cur = cand;
+                    cur_ms = ms;
+                }
+            }
+            return GSI_OK;
+        };
+        GSI_TRY(try_knob([](gsi_batch_opts &o, int32_t v) { o.seeds_per_item = v; }, {32, 64, 128}));
+        GSI_TRY(try_knob([](gsi_batch_opts &o, int32_t v) { o.item_rows = v; }, {512, 1024, 2048}));
+        GSI_TRY(try_knob([](gsi_batch_opts &o, int32_t v) { o.isect = v; },
+                         {GSI_ISECT_BSEARCH, GSI_ISECT_MERGE, GSI_ISECT_BITMAP}));
+        GSI_TRY(try_knob(
+            [](gsi_batch_opts &o, int32_t v) {
+                o.block_threads = v / 10;
+                o.rows_per_thread = v % 10;
+            },
+            {2562, 2561, 1282, 1281}));
+        *best = cur;
+        best->stats = opts ? opts->stats : nullptr;
+        if (best_ms) *best_ms = cur_ms;
+        if (trials) *trials = runs;
+        return GSI_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("gsi_batch_autotune_full: host allocation failed");
+        return GSI_ENOMEM;
+    } catch (...) {
+        set_error("gsi_batch_autotune_full: unexpected host exception");
+        return GSI_ECUDA;
+    }
+}
+
 // ------------------------------------------------------------------ server
+// Admission by intermediate-table memory.  Every request carries an estimate
+// of its first intermediate table: the fewest directed data edges that match
+// one of its query edges by (label of one end, label of the other, edge
+// label), times two int32 columns.  That is Alg. 4's preallocation bound of
+// a first join step along that edge before filtering, and the planner
+// usually starts where matches are scarce.  A batch reserves the sum of its
+// requests' estimates times ADMIT_GROWTH (later steps' tables), each at least
+// ADMIT_MIN_REQUEST (room for its result rows), and in all at least
+// ADMIT_MIN_BYTES (a work area that fills every SM), out of the server's
+// memory budget, allocates its work area at that size from the stream-
+// ordered pool, and returns the reservation when its results are out.  A
+// slot takes pending requests in arrival order while their reservation fits
+// what the other slots leave free; when nothing fits it waits for a batch to
+// finish.  A request too large for the budget on its own runs alone.
+namespace {
+constexpr uint64_t ADMIT_GROWTH = 16;
+constexpr uint64_t ADMIT_MIN_BYTES = 4ull << 30;
+constexpr uint64_t ADMIT_MIN_REQUEST = 1ull << 20;    // a request's share of a batch's result area, at least
+constexpr size_t ADMIT_MAX_BATCH = 2048;              // requests per batch when max_batch is 0
+
+// Directed edge counts per (label rank of v, label rank of w, edge label) of
+// the CSR: one thread per vertex of the label-grouped order, one atomic per
+// run of equal neighbour labels (lists are sorted by neighbour label).
+__global__ void k_pair_counts(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cl,
+                              const int32_t *__restrict__ gperm, int64_t np, const int64_t *__restrict__ goff,
+                              int LV, int L, unsigned long long *tab) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = gperm[p];
+        if (v < 0) continue;
+        int lo = 0, hi = LV - 1;                    // largest r with goff[r] <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (goff[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        for (int l = 0; l < L; ++l) {
+            const uint64_t seg = (uint64_t)v * (uint64_t)L + (uint64_t)l;
+            uint32_t q = off[seg];
+            const uint32_t e = off[seg + 1];
+            while (q < e) {
+                const uint16_t r2 = cl[q];
+                uint32_t q2 = q + 1;
+                while (q2 < e && cl[q2] == r2) ++q2;
+                atomicAdd(tab + ((uint64_t)lo * (uint64_t)LV + r2) * (uint64_t)L + (uint64_t)l,
+                          (unsigned long long)(q2 - q));
+                q = q2;
+            }
+        }
+    }
+}
+}  // namespace
+
 struct gsi_server {
     gsi_graph *g = nullptr;
     gsi_server_opts opts;
@@ -293,6 +432,7 @@ struct gsi_server {
         gsi_result *res = nullptr;
         double latency_ms = 0;
         bool cancelled = false;
+        uint64_t est = 0;                 // estimated first intermediate table (bytes)
     };
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -300,17 +440,45 @@ struct gsi_server {
     std::map<uint64_t, std::shared_ptr<Req>> all;
     uint64_t next_ticket = 1;
     bool stop = false;
+    uint64_t reserved = 0;                // budget held by running batches
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
-    std::vector<BatchWorkspace> ws;        // one per slot (empty when batching is off)
+    std::vector<uint64_t> pair;           // directed edge counts [LV][LV][L]; empty: no estimates
 };
 
+namespace {
+uint64_t estimate_bytes(const gsi_server *s, const QueryGraph &q) {
+    const gsi_graph *g = s->g;
+    if (s->pair.empty() || q.qm == 0) return (uint64_t)q.k * 4;     // a single vertex: its candidates
+    uint64_t best = UINT64_MAX;
+    for (int e = 0; e < q.qm; ++e) {
+        const int32_t ra = g->label_rank(q.vl[q.src[e]]), rb = g->label_rank(q.vl[q.dst[e]]);
+        const int32_t l = q.lab[e];
+        uint64_t c = 0;
+        if (ra >= 0 && rb >= 0 && l >= 0 && l < g->L)
+            c = s->pair[((uint64_t)ra * (uint64_t)g->LV + (uint64_t)rb) * (uint64_t)g->L + (uint64_t)l];
+        best = std::min(best, c);
+    }
+    return best * 8;
+}
+
+// A request's part of a batch reservation: its estimate grown for the later
+// steps, at least ADMIT_MIN_REQUEST (its rows in the result area).
+uint64_t request_need(uint64_t est) {
+    const uint64_t grown = est > UINT64_MAX / ADMIT_GROWTH ? UINT64_MAX : est * ADMIT_GROWTH;
+    return std::max(grown, ADMIT_MIN_REQUEST);
+}
+// What a batch whose requests need `need_sum` in total reserves.
+uint64_t reservation(uint64_t need_sum, uint64_t budget) { return std::min(budget, std::max(need_sum, ADMIT_MIN_BYTES)); }
+}  // namespace
+
 // The work of one slot's take: requests one by one on the plain path, or as
-// one batch.
+// one batch in a work area of `reserve` bytes (allocated here, stream-ordered,
+// and released once the results are gathered out of it).
 template <class Publish>
-static void serve_batch(gsi_server *s, cudaStream_t st, uint64_t share, size_t max_batch, size_t min_batch,
-                        BatchWorkspace &ws, std::vector<std::shared_ptr<gsi_server::Req>> &batch,
-                        std::vector<gsi_result *> &res, std::vector<gsi_status> &sts, Publish &publish) {
+static void serve_batch(gsi_server *s, cudaStream_t st, uint64_t reserve, size_t max_batch, size_t min_batch,
+                        std::vector<std::shared_ptr<gsi_server::Req>> &batch, std::vector<gsi_result *> &res,
+                        std::vector<gsi_status> &sts, Publish &publish) {
     if (max_batch == 1 || batch.size() < min_batch) {
         // too few requests to fill the GPU with (query, seed range) items:
         // one query at a time on the plain path, every step on all SMs
@@ -320,11 +488,20 @@ static void serve_batch(gsi_server *s, cudaStream_t st, uint64_t share, size_t m
             o.stream = st;
             o.row_cap = s->opts.row_cap;
             o.count_only = s->opts.count_only;
-            o.mem_budget = share;
+            o.mem_budget = reserve;
             sts[i] = run_query(s->g, batch[i]->q, o, &res[i]);
             publish(i, i + 1);
         }
         return;
+    }
+    BatchWorkspace ws;
+    ws.result_bytes = (reserve / 5) / 256 * 256;
+    ws.arena_bytes = (reserve - ws.result_bytes) / 256 * 256;
+    if (cudaMallocAsync((void **)&ws.arena, ws.arena_bytes, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&ws.result, ws.result_bytes, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (ws.arena) cudaFreeAsync(ws.arena, st);
+        ws = BatchWorkspace();             // the batch reserves its own memory
     }
     std::vector<BatchPlan> plans(batch.size());
     for (size_t i = 0; i < batch.size(); ++i) plans[i].q = batch[i]->q;
@@ -332,48 +509,74 @@ static void serve_batch(gsi_server *s, cudaStream_t st, uint64_t share, size_t m
     std::memset(&bo, 0, sizeof bo);
     bo.stream = st;
     bo.row_cap = s->opts.row_cap;
-    bo.mem_budget = share;
+    bo.mem_budget = reserve;
     bo.count_only = s->opts.count_only;
     bo.seeds_per_item = s->opts.seeds_per_item;
     bo.item_rows = s->opts.item_rows;
+    bo.isect = s->opts.isect;
+    bo.rows_per_thread = s->opts.rows_per_thread;
+    bo.block_threads = s->opts.block_threads;
     gsi_status rc = batch_execute(s->g, plans, bo, res, sts, ws.arena ? &ws : nullptr);
+    if (ws.arena) cudaFreeAsync(ws.arena, st);      // results were gathered into their own buffers
+    if (ws.result) cudaFreeAsync(ws.result, st);
     if (rc != GSI_OK)
         for (size_t i = 0; i < batch.size(); ++i)
             if (sts[i] == GSI_OK && !res[i]) sts[i] = rc;
     publish(0, batch.size());
 }
 
-// One slot: a worker thread with its own stream and an equal share of the
-// memory budget.  It takes every pending request (up to max_batch) as one
-// batch, so requests that arrived while other batches were on the GPU are
-// admitted as soon as a slot frees; batches of different slots overlap on
-// the device.  With max_batch == 1, or fewer than min_batch requests pending,
-// a slot runs one query at a time on the plain path.
+// One slot: a worker thread with its own stream.  It takes pending requests
+// in arrival order (up to max_batch) while the batch's reservation fits the
+// memory the other slots leave free, so requests that arrived while other
+// batches were on the GPU are admitted as soon as a slot and memory free up;
+// batches of different slots overlap on the device.  With max_batch == 1, or
+// fewer than min_batch requests taken, a slot runs one query at a time on the
+// plain path.
 static void server_worker(gsi_server *s, int idx) {
     cudaSetDevice(s->g->device);
     cudaStream_t st = s->streams[idx];
-    const uint64_t share = s->opts.mem_budget / (uint64_t)std::max(1, s->opts.n_streams);
-    const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : (size_t)1 << 30;
+    const uint64_t budget = s->opts.mem_budget;
+    const size_t max_batch = s->opts.max_batch > 0 ? (size_t)s->opts.max_batch : ADMIT_MAX_BATCH;
     const size_t min_batch = s->opts.min_batch > 0 ? (size_t)s->opts.min_batch : 16;
-    // the slot's batch workspace, reserved by gsi_server_create (results are
-    // gathered out of it, so it is reused at once)
-    BatchWorkspace &ws = s->ws[idx];
     for (;;) {
         std::vector<std::shared_ptr<gsi_server::Req>> batch;
         bool cancelled = false;
+        uint64_t reserve = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            // work to do and memory for at least the first request
+            auto admissible = [&] {
+                while (!s->queue.empty() && s->queue.front()->cancelled) {
+                    s->queue.front()->status = GSI_ECANCELLED;
+                    s->queue.pop_front();
+                    cancelled = true;
+                }
+                if (s->queue.empty()) return false;
+                const uint64_t need = reservation(request_need(s->queue.front()->est), budget);
+                return s->reserved == 0 || s->reserved + need <= budget;
+            };
+            s->cv_work.wait(lk, [&] { return s->stop || admissible(); });
             if (s->stop && s->queue.empty()) return;
+            uint64_t need_sum = 0;
             while (!s->queue.empty() && batch.size() < max_batch) {
                 auto r = s->queue.front();
-                s->queue.pop_front();
                 if (r->cancelled) {
                     r->status = GSI_ECANCELLED;
+                    s->queue.pop_front();
                     cancelled = true;
                     continue;
                 }
+                const uint64_t need = reservation(need_sum + request_need(r->est), budget);
+                if (!batch.empty() && s->reserved + need > budget) break;     // arrival order: wait for memory
+                need_sum += request_need(r->est);
                 batch.push_back(r);
+                s->queue.pop_front();
+            }
+            if (!batch.empty()) {
+                reserve = reservation(need_sum, budget);
+                if (s->reserved + reserve > budget)      // a request larger than what is free runs alone
+                    reserve = budget > s->reserved ? budget - s->reserved : reserve;
+                s->reserved += reserve;
             }
         }
         if (cancelled) s->cv_done.notify_all();     // their pollers need not wait for this batch
@@ -400,7 +603,7 @@ static void server_worker(gsi_server *s, int idx) {
             s->cv_done.notify_all();
         };
         try {
-            serve_batch(s, st, share, max_batch, min_batch, ws, batch, res, sts, publish);
+            serve_batch(s, st, reserve, max_batch, min_batch, batch, res, sts, publish);
         } catch (...) {
             // a host exception (allocation) must not leave the thread: the
             // requests not yet answered fail, and results made for them are freed
@@ -420,6 +623,11 @@ static void server_worker(gsi_server *s, int idx) {
             }
             publish(published, batch.size());
         }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->reserved -= reserve;
+        }
+        s->cv_work.notify_all();                     // memory freed: waiting slots may admit
     }
 }
 
@@ -435,11 +643,43 @@ static void server_teardown(gsi_server *s) {
     for (auto &kv : s->all)
         if (kv.second->res) gsi_result_destroy(kv.second->res);
     for (auto st : s->streams) cudaStreamDestroy(st);
-    for (BatchWorkspace &w : s->ws) {
-        if (w.arena) cudaFree(w.arena);
-        if (w.result) cudaFree(w.result);
-    }
     delete s;
+}
+
+// The directed edge counts per (label, label, edge label) behind the
+// admission estimates, when the table stays small.
+static gsi_status pair_counts(gsi_server *s) {
+    gsi_graph *g = s->g;
+    const uint64_t cells = (uint64_t)g->LV * (uint64_t)g->LV * (uint64_t)g->L;
+    if (g->m == 0 || g->np == 0 || cells > (1ull << 24)) return GSI_OK;      // no estimates: minimal reservations
+    unsigned long long *tab = nullptr;
+    int64_t *goff = nullptr;
+    cudaStream_t st = s->streams[0];
+    GSI_CUDA_TRY(cudaMallocAsync(&tab, cells * 8, st));
+    gsi_status rc = GSI_OK;
+    if (cudaMallocAsync(&goff, sizeof(int64_t) * g->goff.size(), st) != cudaSuccess ||
+        cudaMemsetAsync(tab, 0, cells * 8, st) != cudaSuccess ||
+        cudaMemcpyAsync(goff, g->goff.data(), sizeof(int64_t) * g->goff.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) {
+        set_error("gsi_server_create: pair-count table setup failed");
+        rc = GSI_ECUDA;
+    }
+    if (rc == GSI_OK) {
+        const int blocks = (int)std::min<int64_t>((g->np + 255) / 256, 4096);
+        k_pair_counts<<<blocks, 256, 0, st>>>(g->off, g->cl, g->gperm, g->np, goff, g->LV, g->L, tab);
+        s->pair.resize(cells);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(s->pair.data(), tab, cells * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("gsi_server_create: pair-count kernel failed");
+            s->pair.clear();
+            rc = GSI_ECUDA;
+        }
+    }
+    cudaFreeAsync(tab, st);
+    if (goff) cudaFreeAsync(goff, st);
+    cudaStreamSynchronize(st);
+    return rc;
 }
 
 static gsi_status server_start(gsi_server *s) {
@@ -454,21 +694,7 @@ static gsi_status server_start(gsi_server *s) {
         GSI_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         s->streams.push_back(st);
     }
-    // each slot's batch workspace, reserved here so that no request waits for it
-    s->ws.assign((size_t)s->opts.n_streams, BatchWorkspace());
-    if (s->opts.max_batch != 1) {
-        const uint64_t share = s->opts.mem_budget / (uint64_t)s->opts.n_streams;
-        for (BatchWorkspace &w : s->ws) {
-            w.result_bytes = (share / 5) / 256 * 256;
-            w.arena_bytes = (share - w.result_bytes) / 256 * 256;
-            if (cudaMalloc(&w.arena, w.arena_bytes) != cudaSuccess ||
-                cudaMalloc(&w.result, w.result_bytes) != cudaSuccess) {
-                if (w.arena) cudaFree(w.arena);           // batches then reserve their own memory
-                w = BatchWorkspace();
-                (void)cudaGetLastError();
-            }
-        }
-    }
+    GSI_TRY(pair_counts(s));
     for (int i = 0; i < s->opts.n_streams; ++i) s->workers.emplace_back(server_worker, s, i);
     return GSI_OK;
 }
@@ -511,6 +737,7 @@ extern "C" gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, 
     try {
         auto r = std::make_shared<gsi_server::Req>();
         GSI_TRY(validate_query(q->vlab, q->k, q->src, q->dst, q->elab, q->qm, &r->q));
+        r->est = estimate_bytes(s, r->q);
         r->t_submit = std::chrono::steady_clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -527,6 +754,22 @@ extern "C" gsi_status gsi_server_submit(gsi_server *s, const gsi_query_desc *q, 
     } catch (...) {
         set_error("gsi_server_submit: unexpected host exception");
         return GSI_ECUDA;
+    }
+}
+
+extern "C" gsi_status gsi_server_estimate(gsi_server *s, const gsi_query_desc *q, uint64_t *bytes) {
+    if (!s || !q || !bytes) {
+        set_error("gsi_server_estimate: null argument");
+        return GSI_EINVAL;
+    }
+    try {
+        QueryGraph qg;
+        GSI_TRY(validate_query(q->vlab, q->k, q->src, q->dst, q->elab, q->qm, &qg));
+        *bytes = estimate_bytes(s, qg);
+        return GSI_OK;
+    } catch (...) {
+        set_error("gsi_server_estimate: host allocation failed");
+        return GSI_ENOMEM;
     }
 }
 

@@ -19,6 +19,7 @@ from . import _build
 GSI_OK, GSI_EINVAL, GSI_ENOMEM, GSI_ECAPPED, GSI_ETIMEOUT, GSI_ECANCELLED, GSI_ECUDA, GSI_EBUSY = range(8)
 GSI_ISOMORPHISM, GSI_HOMOMORPHISM = 0, 1
 GSI_EDGE_HOST_ONLY = 1
+GSI_ISECT_BSEARCH, GSI_ISECT_MERGE, GSI_ISECT_BITMAP = 0, 1, 2
 STATUS_NAMES = {0: "GSI_OK", 1: "GSI_EINVAL", 2: "GSI_ENOMEM", 3: "GSI_ECAPPED", 4: "GSI_ETIMEOUT",
                 5: "GSI_ECANCELLED", 6: "GSI_ECUDA", 7: "GSI_EBUSY"}
 MAX_QUERY_VERTICES = 32
@@ -26,9 +27,9 @@ SIG_WORDS = 16
 
 EXPORTED = [
     "gsi_graph_create", "gsi_graph_destroy", "gsi_graph_get_info", "gsi_graph_export", "gsi_graph_label_freq",
-    "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_destroy",
+    "gsi_query_run", "gsi_result_count", "gsi_result_columns", "gsi_result_copy", "gsi_result_copy_async", "gsi_result_destroy", "gsi_server_estimate",
     "gsi_filter", "gsi_query_signatures", "gsi_join_step", "gsi_join_step_noalloc", "gsi_plan_order",
-    "gsi_batch_run", "gsi_batch_autotune", "gsi_batch_prepare", "gsi_batch_replay", "gsi_batch_destroy", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
+    "gsi_batch_run", "gsi_batch_autotune", "gsi_batch_autotune_full", "gsi_batch_prepare", "gsi_batch_replay", "gsi_batch_destroy", "gsi_server_create", "gsi_server_submit", "gsi_server_poll", "gsi_server_cancel",
     "gsi_server_destroy", "gsi_last_error", "gsi_version", "gsi_selftest_wait_timeout",
     "gsi_edge_graph_create", "gsi_edge_graph_destroy", "gsi_edge_graph_line", "gsi_edge_graph_device",
     "gsi_edge_query_line", "gsi_edge_query_run",
@@ -58,7 +59,7 @@ class c_stats(ctypes.Structure):
                 ("join_bytes", ctypes.c_uint64), ("join_items", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
                 ("peak_bytes", ctypes.c_uint64), ("kernels", ctypes.c_uint64), ("host_driven", ctypes.c_uint64),
                 ("cand", ctypes.c_uint64 * 32), ("order", ctypes.c_int32 * 32),
-                ("k", ctypes.c_int32)]
+                ("k", ctypes.c_int32), ("join_bytes_listwise", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("cand", "order")}
@@ -83,13 +84,15 @@ class c_query_desc(ctypes.Structure):
 class c_batch_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
                 ("count_only", ctypes.c_int32), ("stats", ctypes.POINTER(c_stats)),
-                ("seeds_per_item", ctypes.c_int32), ("item_rows", ctypes.c_int32)]
+                ("seeds_per_item", ctypes.c_int32), ("item_rows", ctypes.c_int32), ("isect", ctypes.c_int32),
+                ("rows_per_thread", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
 
 class c_server_opts(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_uint64), ("n_streams", ctypes.c_int32), ("row_cap", ctypes.c_uint64),
                 ("count_only", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("seeds_per_item", ctypes.c_int32),
-                ("item_rows", ctypes.c_int32), ("min_batch", ctypes.c_int32)]
+                ("item_rows", ctypes.c_int32), ("min_batch", ctypes.c_int32), ("isect", ctypes.c_int32),
+                ("rows_per_thread", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
 
 _lib = None
@@ -136,6 +139,8 @@ def load(build_if_missing: bool = False):
     L.gsi_result_columns.restype = st
     L.gsi_result_copy.argtypes = [VP, VP, ctypes.c_uint64, U64P]
     L.gsi_result_copy.restype = st
+    L.gsi_result_copy_async.argtypes = [VP, VP, ctypes.c_uint64, U64P, VP]
+    L.gsi_result_copy_async.restype = st
     L.gsi_result_destroy.argtypes = [VP]
     L.gsi_result_destroy.restype = None
     L.gsi_filter.argtypes = [VP, I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int32, VP, VP, VP]
@@ -155,6 +160,10 @@ def load(build_if_missing: bool = False):
     L.gsi_batch_run.restype = st
     L.gsi_batch_autotune.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
                                      I32P, I32P, ctypes.POINTER(ctypes.c_double)]
+    L.gsi_batch_autotune_full.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32,
+                                          ctypes.POINTER(c_batch_opts), ctypes.POINTER(c_batch_opts),
+                                          ctypes.POINTER(ctypes.c_double), I32P]
+    L.gsi_batch_autotune_full.restype = st
     L.gsi_batch_autotune.restype = st
     L.gsi_batch_prepare.argtypes = [VP, ctypes.POINTER(c_query_desc), ctypes.c_int32, ctypes.POINTER(c_batch_opts),
                                     ctypes.POINTER(VP), I32P]
@@ -172,6 +181,8 @@ def load(build_if_missing: bool = False):
     L.gsi_server_poll.restype = st
     L.gsi_server_cancel.argtypes = [VP, ctypes.c_uint64]
     L.gsi_server_cancel.restype = st
+    L.gsi_server_estimate.argtypes = [VP, ctypes.POINTER(c_query_desc), U64P]
+    L.gsi_server_estimate.restype = st
     L.gsi_server_destroy.argtypes = [VP]
     L.gsi_server_destroy.restype = None
     L.gsi_edge_graph_create.argtypes = [I32P, ctypes.c_int32, I32P, I32P, I32P, ctypes.c_int64,
@@ -277,6 +288,14 @@ class Result:
         rows = ctypes.c_uint64()
         rc = _check(load().gsi_result_copy(self._h, ptr, max_rows, ctypes.byref(rows)), "gsi_result_copy",
                     ok=(GSI_OK, GSI_ECAPPED))
+        return int(rows.value), rc == GSI_ECAPPED
+
+    def copy_to_async(self, ptr: int, max_rows: int, stream=None) -> tuple[int, bool]:
+        """Enqueue the copy on `stream` (torch stream or handle); returns (rows,
+        capped) at once.  Keep the result alive until the copy has completed."""
+        rows = ctypes.c_uint64()
+        rc = _check(load().gsi_result_copy_async(self._h, ptr, max_rows, ctypes.byref(rows), _stream_handle(stream)),
+                    "gsi_result_copy_async", ok=(GSI_OK, GSI_ECAPPED))
         return int(rows.value), rc == GSI_ECAPPED
 
     def rows(self, max_rows: int | None = None) -> np.ndarray:
@@ -406,13 +425,15 @@ class Graph:
         return int(cnt.value)
 
     def batch(self, queries, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
-              stats: c_stats | None = None, seeds_per_item: int = 0, item_rows: int = 0) -> list:
+              stats: c_stats | None = None, seeds_per_item: int = 0, item_rows: int = 0, isect: int = 0,
+              rows_per_thread: int = 0, block_threads: int = 0) -> list:
         qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
         descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
         outs = (VP * len(qas))()
         sts = (ctypes.c_int32 * len(qas))()
         o = c_batch_opts(_stream_handle(stream), row_cap, mem_budget, int(count_only),
-                         ctypes.pointer(stats) if stats is not None else None, seeds_per_item, item_rows)
+                         ctypes.pointer(stats) if stats is not None else None, seeds_per_item, item_rows, isect,
+                         rows_per_thread, block_threads)
         _check(load().gsi_batch_run(self._h, descs, len(qas), ctypes.byref(o), outs, sts), "gsi_batch_run")
         res = []
         for i in range(len(qas)):
@@ -515,14 +536,16 @@ class PreparedBatch:
     """A batch planned once and replayed from a captured CUDA graph (gsi_batch_prepare / gsi_batch_replay)."""
 
     def __init__(self, graph: "Graph", queries, stream=None, row_cap: int = 0, mem_budget: int = 0,
-                 count_only: bool = False, seeds_per_item: int = 0, item_rows: int = 0, counters: bool = False):
+                 count_only: bool = False, seeds_per_item: int = 0, item_rows: int = 0, counters: bool = False,
+                 isect: int = 0, rows_per_thread: int = 0, block_threads: int = 0):
         self._graph = graph
         self._qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
         self._descs = (c_query_desc * len(self._qas))(*[qa.desc() for qa in self._qas])
         self.statuses = (ctypes.c_int32 * len(self._qas))()
         self._probe = c_stats() if counters else None
         o = c_batch_opts(_stream_handle(stream), row_cap, mem_budget, int(count_only),
-                         ctypes.pointer(self._probe) if counters else None, seeds_per_item, item_rows)
+                         ctypes.pointer(self._probe) if counters else None, seeds_per_item, item_rows, isect,
+                         rows_per_thread, block_threads)
         h = VP()
         _check(load().gsi_batch_prepare(graph.handle, self._descs, len(self._qas), ctypes.byref(o), ctypes.byref(h),
                                         self.statuses), "gsi_batch_prepare")
@@ -552,13 +575,29 @@ def batch_autotune(graph: "Graph", queries, stream=None, mem_budget: int = 0) ->
     """Pick the batch work-unit sizes on a calibration batch: (seeds_per_item, item_rows, ms)."""
     qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
     descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
-    o = c_batch_opts(_stream_handle(stream), 0, mem_budget, 0, None, 0, 0)
+    o = c_batch_opts(_stream_handle(stream), 0, mem_budget, 0, None, 0, 0, 0, 0, 0)
     spi = ctypes.c_int32()
     rows = ctypes.c_int32()
     ms = ctypes.c_double()
     _check(load().gsi_batch_autotune(graph.handle, descs, len(qas), ctypes.byref(o), ctypes.byref(spi),
                                      ctypes.byref(rows), ctypes.byref(ms)), "gsi_batch_autotune")
     return int(spi.value), int(rows.value), float(ms.value)
+
+
+def batch_autotune_full(graph: "Graph", queries, stream=None, mem_budget: int = 0) -> dict:
+    """Every batch knob tuned on a calibration batch (gsi_batch_autotune_full):
+    seeds_per_item, item_rows, isect, rows_per_thread, block_threads, ms, trials."""
+    qas = [q if isinstance(q, QueryArrays) else QueryArrays.of(q) for q in queries]
+    descs = (c_query_desc * len(qas))(*[qa.desc() for qa in qas])
+    o = c_batch_opts(_stream_handle(stream), 0, mem_budget, 0, None, 0, 0, 0, 0, 0)
+    best = c_batch_opts()
+    ms = ctypes.c_double()
+    trials = ctypes.c_int32()
+    _check(load().gsi_batch_autotune_full(graph.handle, descs, len(qas), ctypes.byref(o), ctypes.byref(best),
+                                          ctypes.byref(ms), ctypes.byref(trials)), "gsi_batch_autotune_full")
+    return {"seeds_per_item": best.seeds_per_item, "item_rows": best.item_rows, "isect": best.isect,
+            "rows_per_thread": best.rows_per_thread, "block_threads": best.block_threads,
+            "ms": float(ms.value), "trials": int(trials.value)}
 
 
 def query_signatures(q) -> np.ndarray:
@@ -586,11 +625,11 @@ class Server:
 
     def __init__(self, graph: Graph, mem_budget: int = 0, n_streams: int = 2, row_cap: int = 0,
                  count_only: bool = False, max_batch: int = 0, seeds_per_item: int = 0, item_rows: int = 0,
-                 min_batch: int = 0):
+                 min_batch: int = 0, isect: int = 0, rows_per_thread: int = 0, block_threads: int = 0):
         self._graph = graph
         h = VP()
         o = c_server_opts(mem_budget, n_streams, row_cap, int(count_only), max_batch, seeds_per_item, item_rows,
-                          min_batch)
+                          min_batch, isect, rows_per_thread, block_threads)
         _check(load().gsi_server_create(graph.handle, ctypes.byref(o), ctypes.byref(h)), "gsi_server_create")
         self._h = h.value
 
@@ -613,6 +652,14 @@ class Server:
 
     def cancel(self, ticket: int):
         _check(load().gsi_server_cancel(self._h, ticket), "gsi_server_cancel")
+
+    def estimate(self, q) -> int:
+        """Admission estimate of a query's intermediate-table bytes."""
+        qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
+        b = ctypes.c_uint64()
+        d = qa.desc()
+        _check(load().gsi_server_estimate(self._h, ctypes.byref(d), ctypes.byref(b)), "gsi_server_estimate")
+        return int(b.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -162,9 +162,12 @@ def test_header_constants_match_the_binding(pkg):
     assert fields("c_query_opts") == ["stream", "row_cap", "mem_budget", "count_only", "semantics", "order", "stats",
                                       "host_driven"]
     assert fields("c_batch_opts") == ["stream", "row_cap", "mem_budget", "count_only", "stats", "seeds_per_item",
-                                      "item_rows"]
+                                      "item_rows", "isect", "rows_per_thread", "block_threads"]
     assert fields("c_server_opts") == ["mem_budget", "n_streams", "row_cap", "count_only", "max_batch",
-                                       "seeds_per_item", "item_rows", "min_batch"]
+                                       "seeds_per_item", "item_rows", "min_batch", "isect", "rows_per_thread",
+                                       "block_threads"]
+    for name in ("GSI_ISECT_BSEARCH", "GSI_ISECT_MERGE", "GSI_ISECT_BITMAP"):
+        assert defines[name] == getattr(pkg, name), name
     for st, members in (("gsi_query_opts", fields("c_query_opts")), ("gsi_batch_opts", fields("c_batch_opts")),
                         ("gsi_server_opts", fields("c_server_opts")), ("gsi_graph_opts", fields("c_graph_opts")),
                         ("gsi_graph_info", fields("c_graph_info")), ("gsi_stats", fields("c_stats")),

@@ -198,3 +198,53 @@ def test_prepared_batch_statuses_caps_and_small_budget(pkg, world):
     pb = pkg.PreparedBatch(G, qs[:12], mem_budget=1 << 20)  # no slice fits: every query on the plain path
     assert [r.count for r in pb.run()] == ref
     pb.close()
+
+
+@pytest.fixture(scope="module")
+def dense_world(pkg):
+    """Dense walk queries (|E| up to 2k) on a small R-MAT graph: most join
+    steps have two or more linking edges, so short rows go through the
+    intersection strategies."""
+    s, d = synth.rmat(43, 12, 40_000)
+    n = 1 << 12
+    g = H.G(synth.labels_zipf(43, 1, n, 8, 1.1), s, d, synth.labels_uniform(43, 2, 40_000, 3))
+    sg = synth.make_graph(g.vlab, g.src, g.dst, g.elab, 3)
+    G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
+    O = oracle.OracleGraph(g.vlab, g.src, g.dst, g.elab)
+    qs = [synth.walk_query(sg, 92, i, 5 + i % 4, dense=True, max_bound=1e6) for i in range(24)]
+    assert sum(q.qm > q.k for q in qs) >= 10
+    wants = [oracle.enumerate_rows(O, q) for q in qs]
+    return G, qs, wants
+
+
+@pytest.mark.parametrize("isect", [0, 1, 2])
+@pytest.mark.parametrize("block_threads,rows_per_thread", [(256, 2), (256, 1), (128, 2), (128, 1)])
+def test_batch_knobs_give_the_oracle_sets(pkg, dense_world, isect, block_threads, rows_per_thread):
+    """Every intersection strategy (binary search, merge, candidate-position
+    bitmap) under every block shape of the batch kernel gives the oracle's
+    embedding sets."""
+    G, qs, wants = dense_world
+    res = G.batch(qs, isect=isect, rows_per_thread=rows_per_thread, block_threads=block_threads)
+    assert sum(w.shape[0] > 0 for w in wants) >= 20
+    for q, r, want in zip(qs, res, wants):
+        assert r.count == want.shape[0]
+        assert np.array_equal(oracle.sort_rows(r.rows()), want)
+
+
+def test_batch_knobs_rejected_when_invalid(pkg, world):
+    g, G, O, qs = world
+    for kw in ({"block_threads": 64}, {"rows_per_thread": 3}, {"isect": 7}):
+        with pytest.raises(pkg.GsiError) as e:
+            G.batch(qs[:2], **kw)
+        assert e.value.status == pkg.GSI_EINVAL
+
+
+def test_full_autotuner_returns_a_valid_setting(pkg, dense_world):
+    G, qs, wants = dense_world
+    best = pkg.batch_autotune_full(G, qs)
+    assert best["seeds_per_item"] in (32, 64, 128) and best["item_rows"] in (512, 1024, 2048)
+    assert best["isect"] in (0, 1, 2) and best["rows_per_thread"] in (1, 2) and best["block_threads"] in (128, 256)
+    assert best["ms"] > 0 and best["trials"] >= 2 * 10
+    res = G.batch(qs, **{k: best[k] for k in ("seeds_per_item", "item_rows", "isect", "rows_per_thread",
+                                              "block_threads")})
+    assert [r.count for r in res] == [w.shape[0] for w in wants]

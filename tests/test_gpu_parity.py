@@ -424,3 +424,45 @@ def test_worked_example_on_gpu(pkg):
     M = np.array([(0, i) for i in range(1, 101)], np.int32)
     cnt, rows = _gpu_step(pkg, G, M, g.vlab == 2, 2, [1, 0], [0, 1])   # linking edges u1u2:a, u0u2:b
     assert cnt == 1 and rows.tolist() == [[0, 100] + facts["buf99_final"]]
+
+
+def test_shared_first_edge_rows_on_a_hub_graph(pkg):
+    """Duplicate removal (Sec. VI-B) in the row pass: rows of a step that share
+    their first-edge vertex share one sub-list lookup and one set of bitmap
+    probes (warp groups found with __match_any_sync, and the per-step memo).
+    On a graph of few hubs with hundreds of leaves each, nearly every warp
+    holds such groups, mixed with rows of other vertices and with long rows
+    (more than 16 candidates) that go to the slot tiles.  Counts and
+    full-set fingerprints equal the oracle's; paths, stars and a triangle
+    with a pendant, so both single- and multi-edge steps run."""
+    rng = np.random.default_rng(606)
+    n, hubs = 2400, 6
+    edges = set()
+    for h in range(hubs):
+        for leaf in rng.choice(np.arange(hubs, n), 70, replace=False):
+            edges.add((h, int(leaf)))
+    while len(edges) < 9000:
+        a, b = (int(x) for x in rng.integers(hubs, n, 2))
+        if a != b:
+            edges.add((min(a, b), max(a, b)))
+    edges = sorted(edges)
+    vlab = np.where(np.arange(n) < hubs, 0, 1 + rng.integers(0, 2, n)).astype(np.int32)
+    elab = rng.integers(0, 2, len(edges)).astype(np.int32)
+    g = H.graph(n, edges, vlab=vlab, elab=elab)
+    G = pkg.Graph(g.vlab, g.src, g.dst, g.elab)
+    O = oracle.OracleGraph(g.vlab, g.src, g.dst, g.elab)
+    queries = [
+        H.query(3, [(0, 1), (1, 2)], vlab=[1, 0, 1], elab=[0, 1]),                 # leaf-hub-leaf
+        H.query(4, [(0, 1), (0, 2), (0, 3)], vlab=[0, 1, 2, 1], elab=[0, 0, 1]),   # hub star
+        H.query(4, [(0, 1), (1, 2), (2, 3)], vlab=[2, 0, 1, 2], elab=[1, 0, 1]),   # path through a hub
+        H.query(4, [(0, 1), (1, 2), (0, 2), (2, 3)], vlab=[0, 1, 2, 1], elab=[0, 1, 0, 1]),
+        H.query(5, [(0, 1), (0, 2), (0, 3), (3, 4)], vlab=[0, 1, 1, 2, 1], elab=[1, 1, 0, 0]),
+    ]
+    nonzero = 0
+    for q in queries:
+        want, fp = oracle.count(O, q)
+        r = G.query(q)
+        assert r.count == want
+        assert oracle.fingerprint(r.rows()) == (want, fp[1], fp[2])
+        nonzero += want > 0
+    assert nonzero >= 4

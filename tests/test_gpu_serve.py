@@ -97,3 +97,36 @@ def test_served_workspace_reuse(pkg, world):
         served = _serve_all(S, qs)
         S.close()
         assert [r.count for r, _ in served] == alone
+
+
+def test_server_estimate_is_the_fewest_matching_edges(pkg, world):
+    """The admission estimate of a query is 8 bytes (two int32 columns) times
+    the fewest directed data edges that match one of its query edges by the
+    labels of both ends and the edge label: counted here with numpy from the
+    edge list."""
+    g, G, qs = world
+    S = pkg.Server(G, mem_budget=8 << 30, n_streams=1)
+    src = np.concatenate([g.src, g.dst])
+    dst = np.concatenate([g.dst, g.src])
+    el = np.concatenate([g.elab, g.elab])
+    for q in qs:
+        want = min(int(((g.vlab[src] == q.vlab[a]) & (g.vlab[dst] == q.vlab[b]) & (el == l)).sum())
+                   for a, b, l in zip(q.src, q.dst, q.elab))
+        assert S.estimate(q) == 8 * want
+    # a label no data vertex carries: nothing can match
+    q = H.query(2, [(0, 1)], vlab=[0, 99], elab=[0])
+    assert S.estimate(q) == 0
+    S.close()
+
+
+@pytest.mark.parametrize("budget", [1 << 30, 4 << 30, 12 << 30])
+def test_served_under_tight_memory_budgets(pkg, world, budget):
+    """Batches reserve their estimated memory from the budget (at least 4 GiB
+    or the whole budget): with room for one batch at a time, or for three,
+    every served result equals the plain path's."""
+    g, G, qs = world
+    alone = [G.query(q).count for q in qs]
+    S = pkg.Server(G, mem_budget=budget, n_streams=3, max_batch=0, min_batch=1)
+    served = _serve_all(S, qs * 3)
+    S.close()
+    assert [r.count for r, _ in served] == alone * 3
