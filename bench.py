@@ -144,8 +144,8 @@ def summarize_clocks(lines) -> dict | None:
             "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"k_query": ("join.cu", "join_tile.cuh", "common.cuh", "scan.cuh", "internal.h"),
-                  "k_batch": ("batch.cu", "join_tile.cuh", "common.cuh", "internal.h")}
+KERNEL_SOURCES = {"k_query": ("join.cu", "join_rows.cuh", "join_tile.cuh", "common.cuh", "scan.cuh", "internal.h"),
+                  "k_batch": ("batch.cu", "join_rows.cuh", "join_tile.cuh", "common.cuh", "internal.h")}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -216,7 +216,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
 
     tuned = {}
     knobs = {}
-    if batched:
+    if batched and args.batch_knobs:
+        # fixed settings (a profiling run reproduces a tuned configuration)
+        names = ("seeds_per_item", "item_rows", "isect", "rows_per_thread", "block_threads")
+        knobs = dict(zip(names, (int(x) for x in args.batch_knobs.split(","))))
+        tuned = dict(knobs, fixed=True)
+    elif batched:
         best = pkg.batch_autotune_full(G, mine[:512], stream=stream, mem_budget=budget)
         knobs = {k: best[k] for k in ("seeds_per_item", "item_rows", "isect", "rows_per_thread", "block_threads")}
         tuned = dict(knobs, calibration_ms=best["ms"], calibration_runs=best["trials"],
@@ -295,7 +300,20 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     filter_bytes = sum(s.filter_bytes for s in stats)
     kernels = sum(s.kernels for s in stats)
     host_driven = sum(s.host_driven for s in stats)
-    join_bytes_lw = sum(s.join_bytes_listwise for s in stats)
+    # the whole-list byte count (another model of the same work) from one
+    # untimed pass of the counting kernel variant, per launch like the roofline
+    join_bytes_lw = 0.0
+    if not batched:
+        lw_stats = []
+        for q in mine:
+            st = pkg.c_stats()
+            r = G.query(q, stream=stream, row_cap=row_cap, stats=st, mem_budget=budget, listwise_bytes=True)
+            r.close()
+            lw_stats.append(st)
+        lw_launches = sum(s.join_launches for s in lw_stats)
+        if lw_launches:
+            join_bytes_lw = sum(s.join_bytes_listwise for s in lw_stats) / lw_launches * \
+                (sum(s.join_launches for s in stats) or 0)
     allv = combine([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
                     float(join_launches), filter_ms, float(filter_bytes), float(kernels), float(join_bytes_lw)],
                    world, device="cuda")
@@ -323,8 +341,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         d2h = 0
         emb = 0
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        t0 = None
+        for rep in range(args.e2e_steps + 1):         # the first pass warms the pools (results outlive a query)
+            if rep == 1:
+                torch.cuda.synchronize()
+                d2h = emb = 0
+                t0 = time.perf_counter()
             if batched:
                 res = G.batch(mine, stream=stream, row_cap=row_cap, **knobs)
                 done = []
@@ -361,6 +383,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                "steps": args.e2e_steps, "ms_per_step": el * 1e3 / args.e2e_steps,
                "queries_per_s": len(mine) * args.e2e_steps / el if el > 0 else None,
                "d2h_gbs": d2h / el / 1e9 if el > 0 else None,
+               "warmup_passes": 1,
                "overlap": "each query's rows copied to pinned host memory on a second stream while the next query runs"}
 
     if rank != 0:
@@ -381,7 +404,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                     "bytes_per_launch": float(allv[:, 9].sum()) / jl if jl else None,
                     "achieved": (float(allv[:, 9].sum()) / jl) / ((jms / jl) * 1e-3) / 1e9 if jl and jms else None,
                     "note": "each linking list N(v,l) counted whole, 8 B to locate it, one 4 B bitmap probe per "
-                            "candidate slot; the roofline above counts label sub-lists and 16 B per list"},
+                            "candidate slot (one untimed pass); the roofline above counts label sub-lists and "
+                            "16 B per list"} if not batched else None,
                 "avg_launch_us": jms / jl * 1e3 if jl else None,
                 "share_of_device_time": jms / (t_max_ms * world) if t_max_ms else None}
     fb, fms = float(allv[:, 7].sum()), float(allv[:, 6].sum())
@@ -623,6 +647,8 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "batched"],
                     help="plain: one query at a time; batched: one gsi_batch_run per step (auto: by workload)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    ap.add_argument("--batch-knobs", default="",
+                    help="batched: seeds_per_item,item_rows,isect,rows_per_thread,block_threads instead of autotuning")
     ap.add_argument("--served-queries", type=int, default=20000, help="prefix of the served arrival stream")
     ap.add_argument("--served-slots", type=int, default=2)
     ap.add_argument("--served-min-batch", type=int, default=0,

@@ -143,7 +143,8 @@ typedef struct {
                                        each linking list N(v,l) read whole,
                                        8 bytes to locate it, one 4-byte bitmap
                                        probe per candidate slot (device-driven
-                                       and batched paths) */
+                                       path of gsi_query_run, when asked by
+                                       gsi_query_opts.listwise_bytes) */
 } gsi_stats;
 
 /* Query semantics.  GSI_ISOMORPHISM: Defs. 2-3 (injective maps).
@@ -168,6 +169,10 @@ typedef struct {
                                 ranges to fit the budget (the path otherwise
                                 taken only when the device-driven arena
                                 overflows) */
+    int32_t listwise_bytes;  /* 1 (with stats): also count the join's bytes
+                                under the whole-list model
+                                (gsi_stats.join_bytes_listwise), in a kernel
+                                variant that is a few percent slower */
 } gsi_query_opts;
 
 /*

@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(const __grid_constant__
             __syncthreads();
             // short rows joined inline, long rows set aside
             unsigned long long abytes = 0, items = 0, lbytes = 0;
-            row_pass<BNT, true, RPT>(a, M, R, 0, (uint64_t)BNT * RPT, out, cap, &cnt_s, lt, &rfail_s, smem, &abytes,
-                                     &items, &lbytes);
+            row_pass<BNT, true, RPT, false>(a, M, R, 0, (uint64_t)BNT * RPT, out, cap, &cnt_s, lt, &rfail_s, smem,
+                                            &abytes, &items, &lbytes);
             if (a.stats) {                       // one add per step of a unit
                 abytes = block_sum<BNT, unsigned long long>(abytes, wt);
                 items = block_sum<BNT, unsigned long long>(items, wt);
@@ -427,12 +427,12 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
     if (stats) {
         GSI_CUDA_TRY(cudaMallocAsync(&L.dstats, 24, st));
     }
-    size_t sm = join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, 1, 1);
+    size_t sm = join_smem(LONG_RMAX, 1, 1);
     for (int i = 0; i < nq; ++i) {
         BatchPlan &p = plans[i];
         if (!p.active) continue;
         for (int t = 1; t < p.k; ++t) {
-            sm = std::max(sm, join_smem(JOIN_NV / JOIN_ROW_WEIGHT + 2, p.steps[t].t, p.steps[t].d));
+            sm = std::max(sm, join_smem(LONG_RMAX, p.steps[t].t, p.steps[t].d));
             sm = std::max(sm, rows_smem(L.nt, p.steps[t].t, L.rpt));
         }
     }
@@ -490,6 +490,7 @@ gsi_status batch_setup(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &pla
             cfg[(size_t)bqs[i].cfg0 + t] =
                 make_join_args(g, p.steps[t], p.bitmaps + (uint64_t)p.order[t] * (uint64_t)g->nwords, co, L.dstats);
             cfg[(size_t)bqs[i].cfg0 + t].isect = o.isect;
+            cfg[(size_t)bqs[i].cfg0 + t].rmax = LONG_RMAX;     // its tiles see long rows only
         }
         // word ranges of the seed bitmap holding about seeds_per_item seeds each
         const uint64_t nw = (uint64_t)g->nwords;

@@ -47,6 +47,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -171,14 +172,14 @@ __device__ __forceinline__ void cta_prefix(const unsigned long long *bsum, unsig
 
 // The long rows of a step (bound above SHORT_MAX) through the candidate-slot
 // tiles: per-CTA slot sums, slot offsets F, the first row of every tile, then
-// the tiles from a counter, with a grid barrier after each phase.  Survivors
+// the tiles dealt round-robin over the CTAs, with a grid barrier after each
+// phase.  Survivors
 // join those of the row pass in st->out.  False when a barrier wait gave up
 // or the partition does not fit (fail bit 1).
 template <int NT, int VT>
 __device__ __forceinline__ bool long_rows_join(const JoinArgs &a, DStep *st, QueryCtl *ctl, const LongTable &lt,
                                                uint64_t L, uint64_t *F, int64_t *part, uint64_t part_cap,
-                                               uint64_t cap, unsigned long long *bsum, unsigned long long *wt,
-                                               unsigned long long *tile_s) {
+                                               uint64_t cap, unsigned long long *bsum, unsigned long long *wt) {
     constexpr int NV = NT * VT;
     const unsigned G = gridDim.x;
     const uint64_t W = (uint64_t)JOIN_ROW_WEIGHT;
@@ -229,25 +230,22 @@ __device__ __forceinline__ bool long_rows_join(const JoinArgs &a, DStep *st, Que
         part[b] = l2;
     }
     if (!grid_barrier(ctl, G)) return false;
-    // the join tiles, taken from a counter
-    for (;;) {
-        if (threadIdx.x == 0) *tile_s = atomicAdd(&st->next_tile, 1ull);
-        __syncthreads();
-        const uint64_t tile = *tile_s;
-        if (tile >= ntiles) break;
+    // the join tiles, dealt round-robin: every tile holds the same number of
+    // candidate slots, so no counter is needed to balance them
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += G) {
+        __syncthreads();                  // the previous tile's readers of shared memory are done
         join_tile<NT, VT, false, true>(a, lt.rows, (int64_t)L, F, total, __ldcg(part + tile), __ldcg(part + tile + 1),
                                        st->out, cap, &st->count, tile, lt.bnd, lt.blo);
     }
     return grid_barrier(ctl, G);
 }
 
-template <int NT, int VT>
+template <int NT, int VT, bool LW>
 __global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cfgs, DStep *steps, int k, QueryCtl *ctl,
                                               const uint32_t *__restrict__ seed_bitmap, int64_t nwords,
                                               unsigned long long *bsum) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long wt[NT / 32];
-    __shared__ unsigned long long tile_s;
     __shared__ __align__(16) JoinArgs a_s;
     const unsigned G = gridDim.x;
     unsigned long long pre, tot;
@@ -309,12 +307,12 @@ __global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cf
         __syncthreads();
         // ---- short rows joined inline, long rows set aside (one pass over M)
         unsigned long long abytes = 0, items = 0, lbytes = 0;
-        row_pass<NT>(a, st->M, R, (uint64_t)blockIdx.x * NT * ROW_RPT, (uint64_t)G * NT * ROW_RPT, st->out, cap,
-                     &st->count, lt, &ctl->fail, smem, &abytes, &items, &lbytes);
+        row_pass<NT, true, ROW_RPT, LW>(a, st->M, R, (uint64_t)blockIdx.x * NT * ROW_RPT, (uint64_t)G * NT * ROW_RPT,
+                                        st->out, cap, &st->count, lt, &ctl->fail, smem, &abytes, &items, &lbytes);
         if (a.stats) {                       // one add per CTA and step
             abytes = block_sum<NT, unsigned long long>(abytes, wt);
             items = block_sum<NT, unsigned long long>(items, wt);
-            lbytes = block_sum<NT, unsigned long long>(lbytes, wt);
+            if (LW) lbytes = block_sum<NT, unsigned long long>(lbytes, wt);
             if (threadIdx.x == 0) {
                 if (abytes) atomicAdd(a.stats, abytes);
                 if (items) atomicAdd(a.stats + 1, items);
@@ -327,12 +325,12 @@ __global__ void __launch_bounds__(NT, 4) k_query(const JoinArgs *__restrict__ cf
         const uint64_t L = __ldcg(lt.count);
         if (L > 0 && !long_rows_join<NT, VT>(a, st, ctl, lt, L, st->S + ll.f_off,
                                              reinterpret_cast<int64_t *>(st->S + ll.part_off), ll.part_cap, cap,
-                                             bsum, wt, &tile_s))
+                                             bsum, wt))
             return;
         if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) {      // survivors written (both models)
             const unsigned long long wbytes = 4ull * (uint64_t)(t + 1) * min((uint64_t)__ldcg(&st->count), cap);
             atomicAdd(a.stats, wbytes);
-            atomicAdd(a.stats + 2, wbytes);
+            if (LW) atomicAdd(a.stats + 2, wbytes);
         }
     }
 }
@@ -464,6 +462,7 @@ gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &s
         cfg[t] = make_join_args(g, steps[t], bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords, co, stats);
         cfg[t].memo = memo;
         cfg[t].memo_n = g->n;
+        cfg[t].rmax = LONG_RMAX;             // the tiles of k_query see long rows only
         sm = std::max(sm, join_smem(cfg[t].rmax, steps[t].t, steps[t].d));
         sm = std::max(sm, rows_smem(JOIN_NT, steps[t].t));
     }
@@ -476,30 +475,34 @@ gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &s
 }
 
 gsi_status launch_query_coop(const gsi_graph *g, int k, const uint32_t *seed_bitmap, size_t sm, void *cfg_dev,
-                             DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out,
+                             DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out, bool listwise,
                              cudaStream_t st) {
+    // the variant that also counts whole-list bytes costs registers: only on request
+    const void *kern = listwise ? (const void *)k_query<JOIN_NT, JOIN_VT, true>
+                                : (const void *)k_query<JOIN_NT, JOIN_VT, false>;
     int dev = 0;
     cudaGetDevice(&dev);
     // occupancy depends only on the dynamic shared memory: looked up once per
     // (device, size), as are the function attribute and the SM count
     static std::mutex mu;
-    static std::map<std::pair<int, size_t>, int> occ;
+    static std::map<std::tuple<int, size_t, bool>, int> occ;
     static int nsm[64];
     int per_sm = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev >= 0 && dev < 64 && !nsm[dev]) {
-            GSI_CUDA_TRY(cudaFuncSetAttribute(k_query<JOIN_NT, JOIN_VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              200 * 1024));
+            GSI_CUDA_TRY(cudaFuncSetAttribute(k_query<JOIN_NT, JOIN_VT, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+            GSI_CUDA_TRY(cudaFuncSetAttribute(k_query<JOIN_NT, JOIN_VT, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
             GSI_CUDA_TRY(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
         }
-        auto it = occ.find({dev, sm});
+        auto it = occ.find({dev, sm, listwise});
         if (it != occ.end()) {
             per_sm = it->second;
         } else {
-            GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<JOIN_NT, JOIN_VT>, JOIN_NT,
-                                                                       sm));
-            occ[{dev, sm}] = per_sm;
+            GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JOIN_NT, sm));
+            occ[{dev, sm, listwise}] = per_sm;
         }
     }
     if (per_sm < 1) {
@@ -514,8 +517,7 @@ gsi_status launch_query_coop(const gsi_graph *g, int k, const uint32_t *seed_bit
     int64_t nwords = g->nwords;
     void *args[] = {(void *)&cfgp, (void *)&dsteps, (void *)&k, (void *)&ctl, (void *)&seed_bitmap, (void *)&nwords,
                     (void *)&bsum};
-    GSI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_query<JOIN_NT, JOIN_VT>, dim3(grid), dim3(JOIN_NT), args,
-                                             sm, st));
+    GSI_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(JOIN_NT), args, sm, st));
     return GSI_OK;
 }
 

@@ -45,6 +45,9 @@
 namespace gsi {
 
 constexpr int SHORT_MAX = 16;     // rows with at most this many candidates are joined inline
+// Rows of one slot tile of long rows: every long row spans at least
+// SHORT_MAX + 1 + W slots, plus a partial row at each end of the tile.
+constexpr int LONG_RMAX = JOIN_NV / (SHORT_MAX + 1 + JOIN_ROW_WEIGHT) + 2;
 constexpr int MEMO_EDGES = 4;     // linking edges of a step with a sub-list memo
 constexpr uint32_t MEMO_TAG_SHIFT = 59;
 
@@ -167,7 +170,7 @@ __device__ __forceinline__ uint32_t subtract_row(const JoinArgs &a, const int32_
 // first *best candidates when best <= SHORT_MAX.  Lanes whose rows share the
 // first-edge vertex of a single-edge step share the lookup and the bitmap
 // probes (every lane of the warp must call this together).
-template <bool DR>
+template <bool DR, bool LW = true>
 __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *row, bool valid, int lane,
                                              uint32_t *best_out, uint32_t *lob_out, int *jb_out,
                                              unsigned long long *abytes, unsigned long long *items,
@@ -191,7 +194,7 @@ __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *r
         if (valid && best <= (uint32_t)SHORT_MAX) mask = subtract_row(a, row, lob, bm);
         if (valid && stats) {
             *abytes += row_alg_bytes(t, 1, best, best);
-            *lbytes += row_list_bytes(t, 1, whole_len(a, 0, v), best);
+            if (LW) *lbytes += row_list_bytes(t, 1, whole_len(a, 0, v), best);
             *items += best;
         }
     } else if (valid) {
@@ -223,10 +226,12 @@ __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *r
             }
         }
         if (stats) {
-            uint64_t wsum = 0;
-            for (int j = 0; j < d; ++j) wsum += whole_len(a, j, row[a.s.col[j]]);
+            if (LW) {
+                uint64_t wsum = 0;
+                for (int j = 0; j < d; ++j) wsum += whole_len(a, j, row[a.s.col[j]]);
+                *lbytes += row_list_bytes(t, d, wsum, best);
+            }
             *abytes += row_alg_bytes(t, d, lsum, best);
-            *lbytes += row_list_bytes(t, d, wsum, best);
             *items += best;
         }
         if (best > 0 && best <= (uint32_t)SHORT_MAX) {
@@ -300,7 +305,7 @@ __device__ __forceinline__ uint32_t row_join(const JoinArgs &a, const int32_t *r
 // lob[q] and mask[q]; rows past nb get best 0.
 constexpr int ROW_C = 8;          // candidate values of a single-edge group loaded in the first round
 
-template <int NT, int RPT>
+template <int NT, int RPT, bool LW = true>
 __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_t *rowv, int nb, int lane,
                                                  uint32_t *best, uint32_t *lob, uint32_t *mask,
                                                  unsigned long long *abytes, unsigned long long *items,
@@ -365,11 +370,13 @@ __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_
         const uint32_t b = __shfl_sync(FULL_MASK, bm[q], leader[q]);
         if (!valid) best[q] = 0;
         mask[q] = (valid && best[q] <= (uint32_t)SHORT_MAX) ? subtract_row(a, rowv + lr * t, lob[q], b) : 0u;
-        if (a.stats) {                                // whole first-edge list, from the group leader
-            const uint32_t whole = __shfl_sync(FULL_MASK, lead[q] ? whole_len(a, 0, v[q]) : 0u, leader[q]);
+        if (a.stats) {
+            if (LW) {                                 // whole first-edge list, from the group leader
+                const uint32_t whole = __shfl_sync(FULL_MASK, lead[q] ? whole_len(a, 0, v[q]) : 0u, leader[q]);
+                if (valid) *lbytes += row_list_bytes(t, 1, whole, best[q]);
+            }
             if (valid) {
                 *abytes += row_alg_bytes(t, 1, best[q], best[q]);
-                *lbytes += row_list_bytes(t, 1, whole, best[q]);
                 *items += best[q];
             }
         }
@@ -384,8 +391,8 @@ __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_
 // full or a bound does not fit its record.  When a.stats is set, adds this
 // thread's algorithmic bytes (rows read, lists located and read; survivors
 // are counted by the caller) to *abytes, the same under the whole-list model
-// to *lbytes, and its candidate slots to *items.
-template <int NT, bool DR = true, int RPT = ROW_RPT>
+// to *lbytes (only when LW), and its candidate slots to *items.
+template <int NT, bool DR = true, int RPT = ROW_RPT, bool LW = true>
 __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64_t first, uint64_t stride,
                          int32_t *__restrict__ out, uint64_t cap, unsigned long long *count, const LongTable &lt,
                          unsigned *fail, unsigned char *smem, unsigned long long *abytes,
@@ -417,7 +424,7 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
         int jb[RPT];
         uint32_t n = 0, nl = 0;
         if (DR && a.s.d == 1) {
-            rows_join_single<NT, RPT>(a, rowv, nb, lane, best, lob, mask, abytes, items, lbytes);
+            rows_join_single<NT, RPT, LW>(a, rowv, nb, lane, best, lob, mask, abytes, items, lbytes);
 #pragma unroll
             for (int q = 0; q < RPT; ++q) jb[q] = 0;
         } else {
@@ -425,7 +432,7 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
             for (int q = 0; q < RPT; ++q) {
                 const int lr = q * NT + (int)threadIdx.x;
                 const bool valid = lr < nb;
-                mask[q] = row_join<false>(a, rowv + (valid ? lr : 0) * t, valid, lane, &best[q], &lob[q], &jb[q],
+                mask[q] = row_join<false, LW>(a, rowv + (valid ? lr : 0) * t, valid, lane, &best[q], &lob[q], &jb[q],
                                           abytes, items, lbytes);
                 if (!valid) best[q] = 0;
             }
@@ -435,16 +442,36 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
             n += __popc(mask[q]);
             nl += best[q] > (uint32_t)SHORT_MAX;
         }
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<NT, uint32_t>(n | (nl << 16), wt, &tot);
+        // one barrier: warp scans, warp totals through shared memory (wt is
+        // written again only after the next batch's staging barrier)
+        uint32_t ex, tot;
+        {
+            const uint32_t v = n | (nl << 16);
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wt[warp] = x;
+            __syncthreads();
+            uint32_t pre = 0;
+            tot = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t y = wt[w];
+                pre += w < warp ? y : 0u;
+                tot += y;
+            }
+            ex = pre + x - v;
+        }
         const uint32_t ntot = tot & 0xffffu, ltot = tot >> 16;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0) {                 // read after the next barrier
             base_s = ntot ? atomicAdd(count, (unsigned long long)ntot) : 0ull;
             lbase_s = ltot ? atomicAdd(lt.count, (unsigned long long)ltot) : 0ull;
         }
-        __syncthreads();
         // long rows to the table
-        {
+        auto copy_long = [&]() {
             unsigned long long li = lbase_s + (ex >> 16);
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
@@ -460,17 +487,18 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
                 }
                 ++li;
             }
-        }
+        };
         if (!write || ntot == 0) {
+            __syncthreads();
+            if (ltot) copy_long();
             __syncthreads();
             continue;
         }
-        // survivors in rounds of CCAP rows: list, then one coalesced run
-        const uint64_t base = base_s;
-        const uint64_t room = cap > base ? cap - base : 0;
-        const uint32_t nrow = (uint32_t)min((uint64_t)ntot, room);
-        for (uint32_t rb = 0; rb < nrow; rb += CCAP) {
-            const uint32_t re = min(nrow, rb + (uint32_t)CCAP);
+        // survivors in rounds of CCAP rows: list, then one coalesced run (the
+        // list needs only this batch's total; the output base arrives with
+        // the first round's barrier)
+        for (uint32_t rb = 0; rb < ntot; rb += CCAP) {
+            const uint32_t re = min(ntot, rb + (uint32_t)CCAP);
             // each thread lists its survivors as (local row, candidate
             // position); the values are then fetched with the loads spread
             // over all threads instead of one serial chain per thread
@@ -485,14 +513,18 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
                 }
             }
             __syncthreads();
+            if (rb == 0 && ltot) copy_long();
             const uint32_t nr0 = re - rb;
             for (uint32_t r = threadIdx.x; r < nr0; r += NT) {
                 const uint32_t e = comp_r[r];
                 comp_w[r] = __ldg(a.ci + lobs[e & 1023u] + (e >> 10));
             }
             __syncthreads();
+            const uint64_t base = base_s;
+            const uint64_t room = cap > base ? cap - base : 0;
+            const uint32_t nrow = (uint32_t)min((uint64_t)ntot, room);
             int32_t *dst = out + (base + rb) * (uint64_t)W1;
-            const uint32_t nr = re - rb;
+            const uint32_t nr = nrow > rb ? min(re, nrow) - rb : 0u;
             if (rs < rpw)
                 for (uint32_t r = (uint32_t)(warp * rpw + rs); r < nr; r += (uint32_t)(NW * rpw)) {
                     const int32_t val = src_col == t ? comp_w[r] : rowv[(int)(comp_r[r] & 1023u) * t + src_col];
@@ -500,7 +532,6 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
                 }
             __syncthreads();
         }
-        if (nrow == 0) __syncthreads();
     }
 }
 

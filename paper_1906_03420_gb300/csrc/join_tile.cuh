@@ -185,10 +185,13 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
 // every step), so they are read through L2 (ld.global.cg) and never through
 // the non-coherent read-only path.
 //
-// With bounds (PRE), the bound scan already found each row's shortest label
-// sub-list: bnd[r] holds its length and linking-edge index (BOUND_LEN_BITS),
-// blo[r] its start.  Staging then reads those instead of searching, and the
-// other linking lists are probed whole with the (label rank, id) key.
+// With bounds (PRE: the long rows set aside by the row pass), each row's
+// shortest label sub-list is already known: bnd[r] holds its length and
+// linking-edge index (BOUND_LEN_BITS), blo[r] its start.  Staging then reads
+// those instead of searching, the other linking lists are probed whole with
+// the (label rank, id) key, and since every such row spans more than
+// SHORT_MAX + W slots a tile holds few rows, so each slot finds its row by a
+// binary search of the staged offsets instead of a block-wide scan.
 template <int NT, int VT, bool TILE_STATS = true, bool PRE = false>
 __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, int64_t R,
                                           const uint64_t *F, uint64_t total, int64_t r_lo,
@@ -220,7 +223,8 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
     const int nr = (int)(r_hi - r_lo + 1);
 
     // ---- stage the tile's rows: values, candidate sub-list, other sub-lists
-    for (int x = threadIdx.x; x < NV; x += NT) rowmap[x] = 0;
+    if (!PRE)
+        for (int x = threadIdx.x; x < NV; x += NT) rowmap[x] = 0;
     for (int lr = threadIdx.x; lr <= nr; lr += NT) Fs[lr] = __ldcg(F + r_lo + lr);
     __syncthreads();
     unsigned long long bytes = 0;
@@ -244,8 +248,6 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
                 lst[(lr * dm1 + q) * 2 + 1] = x1 - x0;
                 ++q;
             }
-            const uint64_t fr = Fs[lr];
-            if (fr > s0 && fr < s1) rowmap[fr - s0] = (uint16_t)lr;
             continue;
         }
         // the row's lists: the shortest label sub-list supplies candidates
@@ -275,7 +277,7 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         if (TILE_STATS && a.stats && fr >= s0) bytes += 4ull * t + 8ull * d + 4ull * (lsum - best);   // row owned by this tile
     }
     __syncthreads();
-    {   // slot -> row: inclusive max-scan of the row-start marks
+    if (!PRE) {   // slot -> row: inclusive max-scan of the row-start marks
         int v[VT];
         int m = 0;
 #pragma unroll
@@ -296,8 +298,8 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < VT; ++k) rowmap[threadIdx.x * VT + k] = (uint16_t)max(ex, v[k]);
+        __syncthreads();
     }
-    __syncthreads();
 
     // ---- candidates: one slot per thread per round, consecutive slots per warp
     int32_t wv[VT];
@@ -310,7 +312,20 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         wv[k] = 0;
         lrv[k] = 0;
         if (s >= s1) continue;
-        const int lr = rowmap[s - s0];
+        int lr;
+        if (PRE) {
+            // long rows only (each holds more than SHORT_MAX + W slots): few
+            // rows per tile, found by a search of the staged offsets
+            int l = 0, h = nr - 1;
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (Fs[mid] <= s) l = mid;
+                else h = mid - 1;
+            }
+            lr = l;
+        } else {
+            lr = rowmap[s - s0];
+        }
         const int64_t p = (int64_t)(s - Fs[lr]) - a.W;
         if (p < 0) continue;            // a row-staging slot
         ++items;

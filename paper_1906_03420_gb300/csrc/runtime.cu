@@ -472,7 +472,7 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     if (rc == GSI_OK) {
         tm.begin(1);
         rc = launch_query_coop(g, k, bitmaps + (uint64_t)order[0] * (uint64_t)g->nwords, smem, cfg_dev, dst, qc, bsum,
-                               &grid, st);
+                               &grid, listwise && stats, st);
         tm.end();
         kernels += 1;
         tiles += (uint64_t)(k - 1);
@@ -564,6 +564,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     x.row_cap = o.row_cap;
     x.count_only = o.count_only;
     x.stats = o.stats;
+    x.listwise = o.listwise_bytes != 0;
     x.res = res.get();
     x.tm.on = o.stats != nullptr;
     x.tm.st = x.st;

@@ -72,7 +72,7 @@ class c_query_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
                 ("count_only", ctypes.c_int32), ("semantics", ctypes.c_int32),
                 ("order", ctypes.POINTER(ctypes.c_int32)), ("stats", ctypes.POINTER(c_stats)),
-                ("host_driven", ctypes.c_int32)]
+                ("host_driven", ctypes.c_int32), ("listwise_bytes", ctypes.c_int32)]
 
 
 class c_query_desc(ctypes.Structure):
@@ -371,7 +371,8 @@ class Graph:
         return out
 
     def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
-              order=None, stats: c_stats | None = None, host_driven: bool = False, semantics: int = 0) -> Result:
+              order=None, stats: c_stats | None = None, host_driven: bool = False, semantics: int = 0,
+              listwise_bytes: bool = False) -> Result:
         qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
         o = c_query_opts()
         o.stream = _stream_handle(stream)
@@ -380,6 +381,7 @@ class Graph:
         o.count_only = int(count_only)
         o.semantics = int(semantics)
         o.host_driven = int(host_driven)
+        o.listwise_bytes = int(listwise_bytes)
         ordr = None
         if order is not None:
             ordr = _i32(order)
@@ -508,7 +510,8 @@ class EdgeGraph:
         return Graph._borrowed(g.value, self.device, self)
 
     def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
-              order=None, stats: c_stats | None = None, host_driven: bool = False) -> Result:
+              order=None, stats: c_stats | None = None, host_driven: bool = False,
+              listwise_bytes: bool = False) -> Result:
         qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
         o = c_query_opts()
         o.stream = _stream_handle(stream)
@@ -516,6 +519,7 @@ class EdgeGraph:
         o.mem_budget = mem_budget
         o.count_only = int(count_only)
         o.host_driven = int(host_driven)
+        o.listwise_bytes = int(listwise_bytes)
         ordr = None
         if order is not None:
             ordr = _i32(order)
