@@ -300,6 +300,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     filter_bytes = sum(s.filter_bytes for s in stats)
     kernels = sum(s.kernels for s in stats)
     host_driven = sum(s.host_driven for s in stats)
+    batch_ms = sum(s.batch_ms for s in stats)           # the batch kernel alone (batched mode)
+    batch_bytes = sum(s.batch_bytes for s in stats)
+    batch_launches = sum(1 for s in stats if s.batch_ms > 0)
     # the whole-list byte count (another model of the same work) from one
     # untimed pass of the counting kernel variant, per launch like the roofline
     join_bytes_lw = 0.0
@@ -315,7 +318,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
             join_bytes_lw = sum(s.join_bytes_listwise for s in lw_stats) / lw_launches * \
                 (sum(s.join_launches for s in stats) or 0)
     allv = combine([dev_ms, float(embeddings), float(len(mine) * args.steps), join_ms, float(join_bytes),
-                    float(join_launches), filter_ms, float(filter_bytes), float(kernels), float(join_bytes_lw)],
+                    float(join_launches), filter_ms, float(filter_bytes), float(kernels), float(join_bytes_lw),
+                    batch_ms, float(batch_bytes), float(batch_launches)],
                    world, device="cuda")
     t_max_ms = float(allv[:, 0].max())
     tot_emb = float(allv[:, 1].sum())
@@ -391,6 +395,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     jb, jms, jl = float(allv[:, 4].sum()), float(allv[:, 3].sum()), float(allv[:, 5].sum())
+    rerun = None
+    if batched:
+        # the batch kernel alone; queries rerun on the plain path are reported beside it
+        rerun = {"queries": int(sum(s.host_driven for s in stats)), "join_ms": jms - float(allv[:, 10].sum()),
+                 "join_bytes": jb - float(allv[:, 11].sum())}
+        jb, jms, jl = float(allv[:, 11].sum()), float(allv[:, 10].sum()), float(allv[:, 12].sum())
     achieved = (jb / jl) / ((jms / jl) * 1e-3) / 1e9 if jl > 0 and jms > 0 else None
     kname = "k_batch" if batched else "k_query"
     traffic, traffic_src = recorded_traffic(kname, args.workload, jb / jl if jl else None)
@@ -407,7 +417,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                             "candidate slot (one untimed pass); the roofline above counts label sub-lists and "
                             "16 B per list"} if not batched else None,
                 "avg_launch_us": jms / jl * 1e3 if jl else None,
-                "share_of_device_time": jms / (t_max_ms * world) if t_max_ms else None}
+                "share_of_device_time": jms / (t_max_ms * world) if t_max_ms else None,
+                "plain_path_reruns": rerun}
     fb, fms = float(allv[:, 7].sum()), float(allv[:, 6].sum())
     cfg = {"workload": args.workload, "graph": w.graph.kind + f" n={w.graph.n} m={w.graph.m}",
            "query_subset": args.queries or "all", "vertex_labels": w.graph.n_vlabels, "edge_labels": w.graph.n_elabels,

@@ -145,6 +145,11 @@ typedef struct {
                                        probe per candidate slot (device-driven
                                        path of gsi_query_run, when asked by
                                        gsi_query_opts.listwise_bytes) */
+    double batch_ms;         /* batches: device time of the batch kernel
+                                alone (included in join_ms, which also holds
+                                queries rerun on the plain path) */
+    uint64_t batch_bytes;    /* batches: the batch kernel's share of
+                                join_bytes */
 } gsi_stats;
 
 /* Query semantics.  GSI_ISOMORPHISM: Defs. 2-3 (injective maps).

@@ -135,6 +135,19 @@ __device__ long long next_unit(const BatchArgs &b) {
     }
 }
 
+// Drops, without a write-back, the L2 lines that lie wholly inside
+// [p, p + bytes): for a CTA's own tables once they have been read for the
+// last time, so that dead rows are not written to HBM when L2 evicts them.
+// The contents become undefined.  Called by all threads between a barrier
+// after the last read and one before the next write of the range.
+template <int NT>
+__device__ __forceinline__ void discard_l2(const void *p, uint64_t bytes) {
+    const uint64_t a = (uint64_t)reinterpret_cast<uintptr_t>(p);
+    const uint64_t end = (a + bytes) & ~127ull;
+    for (uint64_t x = ((a + 127) & ~127ull) + 128ull * threadIdx.x; x < end; x += 128ull * NT)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(x) : "memory");
+}
+
 // One instance per block shape: NT threads per CTA, RPT rows per thread in
 // the row pass (the batched autotuner picks one).
 template <int NT, int RPT>
@@ -281,6 +294,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(const __grid_constant__
                 }
             }
             __syncthreads();
+            discard_l2<BNT>(M, R * (uint64_t)t * 4);    // this step's input is dead
             const uint64_t cnt = cnt_s;
             if (a.stats && threadIdx.x == 0) {   // survivors written (both models)
                 atomicAdd(a.stats, 4ull * (uint64_t)(t + 1) * min(cnt, cap));
@@ -320,6 +334,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(const __grid_constant__
                     const uint64_t n = extra * w;
                     for (uint64_t i = threadIdx.x; i < n; i += BNT) dst[i] = src[i];
                     __syncthreads();
+                    discard_l2<BNT>(src, n * 4);       // the queued rows now live in the spill area
                     if (threadIdx.x == 0) {
                         __threadfence();
                         const unsigned long long s0 = slot_s;
@@ -371,6 +386,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(const __grid_constant__
             for (uint64_t i = threadIdx.x; i < n; i += BNT) dst[i] = __ldcg(M + i);
         }
         __syncthreads();
+        if (!fail_s && rows > 0) discard_l2<BNT>(M, rows * (uint64_t)k * 4);   // copied out
         if (threadIdx.x == 0) {
             atomicAdd(&c->units, 1ull);
             __threadfence();
@@ -643,6 +659,7 @@ gsi_status batch_collect(BatchLaunch &L, gsi_graph *g, std::vector<BatchPlan> &p
         unsigned long long hb[3] = {0, 0, 0};
         if (L.dstats && cudaMemcpy(hb, L.dstats, 24, cudaMemcpyDeviceToHost) != cudaSuccess) hb[0] = hb[1] = hb[2] = 0;
         stats->join_bytes += hb[0];
+        stats->batch_bytes += hb[0];
         stats->join_items += hb[1];
         stats->join_bytes_listwise += hb[2];
         stats->tiles += rctl.units;
@@ -769,6 +786,7 @@ gsi_status batch_run_device(gsi_graph *g, std::vector<BatchPlan> &plans, const g
         float ms = 0;
         if (rc == GSI_OK) cudaEventElapsedTime(&ms, e0, e1);
         stats->join_ms += ms;
+        stats->batch_ms += ms;
         stats->join_launches += L.nitems ? 1 : 0;
         stats->kernels += L.nitems ? 1 : 0;
         cudaEventDestroy(e0);

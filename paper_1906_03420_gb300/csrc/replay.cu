@@ -150,6 +150,7 @@ extern "C" gsi_status gsi_batch_replay(gsi_batch *b, gsi_result **outs, int32_t 
             cudaEventElapsedTime(&jms, b->ev[1], b->ev[2]);
             stats->filter_ms += fms;
             stats->join_ms += jms;
+            stats->batch_ms += jms;
             stats->filter_launches += b->in.fp.ngroups ? 1 : 0;
             stats->join_launches += b->L.nitems ? 1 : 0;
             stats->kernels += (b->in.fp.ngroups ? 1 : 0) + (b->L.nitems ? 1 : 0);

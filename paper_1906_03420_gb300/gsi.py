@@ -59,7 +59,8 @@ class c_stats(ctypes.Structure):
                 ("join_bytes", ctypes.c_uint64), ("join_items", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
                 ("peak_bytes", ctypes.c_uint64), ("kernels", ctypes.c_uint64), ("host_driven", ctypes.c_uint64),
                 ("cand", ctypes.c_uint64 * 32), ("order", ctypes.c_int32 * 32),
-                ("k", ctypes.c_int32), ("join_bytes_listwise", ctypes.c_uint64)]
+                ("k", ctypes.c_int32), ("join_bytes_listwise", ctypes.c_uint64),
+                ("batch_ms", ctypes.c_double), ("batch_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("cand", "order")}
