@@ -515,9 +515,25 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
             __syncthreads();
             if (rb == 0 && ltot) copy_long();
             const uint32_t nr0 = re - rb;
-            for (uint32_t r = threadIdx.x; r < nr0; r += NT) {
-                const uint32_t e = comp_r[r];
-                comp_w[r] = __ldg(a.ci + lobs[e & 1023u] + (e >> 10));
+            {   // four loads in flight per thread (shared reads first, then the list loads)
+                uint32_t r = threadIdx.x;
+                for (; r + 3 * NT < nr0; r += 4 * NT) {
+                    uint32_t idx[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t e = comp_r[r + j * NT];
+                        idx[j] = lobs[e & 1023u] + (e >> 10);
+                    }
+                    int32_t v[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[j] = __ldg(a.ci + idx[j]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) comp_w[r + j * NT] = v[j];
+                }
+                for (; r < nr0; r += NT) {
+                    const uint32_t e = comp_r[r];
+                    comp_w[r] = __ldg(a.ci + lobs[e & 1023u] + (e >> 10));
+                }
             }
             __syncthreads();
             const uint64_t base = base_s;
@@ -525,11 +541,26 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
             const uint32_t nrow = (uint32_t)min((uint64_t)ntot, room);
             int32_t *dst = out + (base + rb) * (uint64_t)W1;
             const uint32_t nr = nrow > rb ? min(re, nrow) - rb : 0u;
-            if (rs < rpw)
-                for (uint32_t r = (uint32_t)(warp * rpw + rs); r < nr; r += (uint32_t)(NW * rpw)) {
+            if (rs < rpw) {
+                // four rows per lane per iteration: the shared reads of all
+                // four are issued before the first store
+                const uint32_t step = (uint32_t)(NW * rpw);
+                uint32_t r = (uint32_t)(warp * rpw + rs);
+                for (; r + 3 * step < nr; r += 4 * step) {
+                    int32_t v[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t rr = r + j * step;
+                        v[j] = src_col == t ? comp_w[rr] : rowv[(int)(comp_r[rr] & 1023u) * t + src_col];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dst[(uint64_t)(r + j * step) * W1 + oc] = v[j];
+                }
+                for (; r < nr; r += step) {
                     const int32_t val = src_col == t ? comp_w[r] : rowv[(int)(comp_r[r] & 1023u) * t + src_col];
                     dst[(uint64_t)r * W1 + oc] = val;
                 }
+            }
             __syncthreads();
         }
     }
