@@ -207,7 +207,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
         total = 0
         for q in mine:
             st = pkg.c_stats() if stats_list is not None else None
-            r = G.query(q, stream=stream, row_cap=row_cap, stats=st, mem_budget=budget)
+            r = G.query(q, stream=stream, row_cap=row_cap, stats=st, mem_budget=budget, no_dedup=args.no_dedup)
             total += r.count
             r.close()
             if st is not None:
@@ -428,7 +428,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
            "row_cap": w.row_cap, "l2": "flushed between timed steps (512 MB write)",
            "materialised": True, "parallelism": f"queries sharded over {world} GPU(s)",
            "launch": ("one prepared batch per step, replayed from a captured CUDA graph (filter + batch kernel)"
-                      if batched else "one query at a time (filter + one cooperative join launch)")}
+                      if batched else "one query at a time (filter + one cooperative join launch)"),
+           "duplicate_removal": not args.no_dedup}
     if edge:
         li = G.line().info()
         cfg["semantics"] = ("edge isomorphism (Sec. VII-A): G's line graph resident on the device, each query's "
@@ -665,6 +666,8 @@ def main():
     ap.add_argument("--served-min-batch", type=int, default=0,
                     help="batching server: fewer pending requests run one by one on the plain path (0 = library default)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-dedup", action="store_true",
+                    help="plain path without duplicate removal (Sec. VI-B), to measure what it saves")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

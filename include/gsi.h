@@ -178,6 +178,11 @@ typedef struct {
                                 under the whole-list model
                                 (gsi_stats.join_bytes_listwise), in a kernel
                                 variant that is a few percent slower */
+    int32_t no_dedup;        /* 1: join without duplicate removal (Sec. VI-B):
+                                every row locates its own sub-lists and
+                                probes the bitmap alone (no warp groups, no
+                                sub-list memo); same results, for measuring
+                                what duplicate removal saves */
 } gsi_query_opts;
 
 /*

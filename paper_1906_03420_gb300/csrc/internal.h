@@ -159,9 +159,11 @@ gsi_status selftest_barrier_timeout(int dev, unsigned long long spin_limit, doub
 // the launch (per-vertex label sub-list locations, see join_rows.cuh), or null.
 int query_memo_tables(const std::vector<JoinStep> &steps, int k);
 gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
-                              const int32_t *order, int count_only, unsigned long long *stats, uint64_t *memo,
+                              const int32_t *order, int count_only, unsigned long long *stats, uint64_t *memo, bool nodedup,
                               void *cfg_host, size_t *smem);
-// listwise: the kernel variant that also counts whole-list bytes (stats[2]).
+// nodedup (configs): rows of single-edge steps are joined one by one (no
+// warp groups, no memo).  listwise (launch): the kernel variant that also
+// counts whole-list bytes (stats[2]).
 gsi_status launch_query_coop(const gsi_graph *g, int k, const uint32_t *seed_bitmap, size_t smem, void *cfg_dev,
                              DStep *dsteps, QueryCtl *ctl, unsigned long long *bsum, int *grid_out, bool listwise,
                              cudaStream_t stream);

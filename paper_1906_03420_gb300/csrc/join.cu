@@ -452,7 +452,7 @@ int query_memo_tables(const std::vector<JoinStep> &steps, int k) {
 }
 
 gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &steps, int k, const uint32_t *bitmaps,
-                              const int32_t *order, int count_only, unsigned long long *stats, uint64_t *memo,
+                              const int32_t *order, int count_only, unsigned long long *stats, uint64_t *memo, bool nodedup,
                               void *cfg_host, size_t *smem) {
     JoinArgs *cfg = static_cast<JoinArgs *>(cfg_host);
     std::memset(cfg, 0, sizeof(JoinArgs));
@@ -460,8 +460,9 @@ gsi_status query_coop_configs(const gsi_graph *g, const std::vector<JoinStep> &s
     for (int t = 1; t < k; ++t) {
         const int co = (t == k - 1) && count_only;
         cfg[t] = make_join_args(g, steps[t], bitmaps + (uint64_t)order[t] * (uint64_t)g->nwords, co, stats);
-        cfg[t].memo = memo;
+        cfg[t].memo = nodedup ? nullptr : memo;
         cfg[t].memo_n = g->n;
+        cfg[t].nodedup = nodedup ? 1 : 0;
         cfg[t].rmax = LONG_RMAX;             // the tiles of k_query see long rows only
         sm = std::max(sm, join_smem(cfg[t].rmax, steps[t].t, steps[t].d));
         sm = std::max(sm, rows_smem(JOIN_NT, steps[t].t));

@@ -423,7 +423,7 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
         uint32_t mask[RPT], best[RPT], lob[RPT];
         int jb[RPT];
         uint32_t n = 0, nl = 0;
-        if (DR && a.s.d == 1) {
+        if (DR && a.s.d == 1 && !a.nodedup) {
             rows_join_single<NT, RPT, LW>(a, rowv, nb, lane, best, lob, mask, abytes, items, lbytes);
 #pragma unroll
             for (int q = 0; q < RPT; ++q) jb[q] = 0;

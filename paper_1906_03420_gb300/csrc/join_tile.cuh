@@ -138,7 +138,7 @@ struct JoinArgs {
     uint64_t *memo;
     int64_t memo_n;
     int32_t isect;              // intersection strategy of short multi-edge rows (ISECT_*)
-    int32_t pad_;
+    int32_t nodedup;            // 1: no duplicate removal in the row pass (no warp groups, no memo)
 };
 
 // How a short row's candidates are intersected with its other linking lists

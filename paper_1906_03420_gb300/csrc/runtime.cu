@@ -397,7 +397,7 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     uint64_t *S = nullptr, *memo = nullptr;
     int32_t *reg[2] = {nullptr, nullptr};
     unsigned char *ctl = nullptr;
-    const uint64_t memo_bytes = (uint64_t)query_memo_tables(steps, k) * (uint64_t)g->n * 8;
+    const uint64_t memo_bytes = nodedup ? 0 : (uint64_t)query_memo_tables(steps, k) * (uint64_t)g->n * 8;
     const size_t ctl_bytes = (join_args_size() * (size_t)k + 255) / 256 * 256 +
                              (sizeof(DStep) * (size_t)k + 255) / 256 * 256 + 256 + 8 * (size_t)QUERY_MAX_CTAS;
     gsi_status rc = dalloc(*this, (void **)&S, s_bytes);
@@ -439,7 +439,7 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     }
     unsigned long long *jstats = stats ? d_scalars + 1 : nullptr;
     size_t smem = 0;
-    rc = query_coop_configs(g, steps, k, bitmaps, order, count_only, jstats, memo, h_stage, &smem);
+    rc = query_coop_configs(g, steps, k, bitmaps, order, count_only, jstats, memo, nodedup, h_stage, &smem);
     if (rc != GSI_OK) {
         release();
         return rc;
@@ -565,6 +565,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     x.count_only = o.count_only;
     x.stats = o.stats;
     x.listwise = o.listwise_bytes != 0;
+    x.nodedup = o.no_dedup != 0;
     x.res = res.get();
     x.tm.on = o.stats != nullptr;
     x.tm.st = x.st;

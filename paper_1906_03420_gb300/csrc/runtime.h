@@ -92,6 +92,7 @@ struct Exec {
     uint64_t row_cap = 0;
     int count_only = 0;
     bool listwise = false;           // count whole-list bytes too (gsi_query_opts.listwise_bytes)
+    bool nodedup = false;            // join without duplicate removal (gsi_query_opts.no_dedup)
     uint64_t join_bytes = 0, join_items = 0, join_bytes_listwise = 0;
     uint64_t kernels = 0;
     bool fell_back = false;          // the query ran host-driven            // kernels launched (scan = 3, partition, join, filter, seed = 3)

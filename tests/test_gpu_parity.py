@@ -461,8 +461,9 @@ def test_shared_first_edge_rows_on_a_hub_graph(pkg):
     nonzero = 0
     for q in queries:
         want, fp = oracle.count(O, q)
-        r = G.query(q)
-        assert r.count == want
-        assert oracle.fingerprint(r.rows()) == (want, fp[1], fp[2])
+        for no_dedup in (False, True):      # with and without duplicate removal: the same set
+            r = G.query(q, no_dedup=no_dedup)
+            assert r.count == want
+            assert oracle.fingerprint(r.rows()) == (want, fp[1], fp[2])
         nonzero += want > 0
     assert nonzero >= 4

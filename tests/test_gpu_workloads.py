@@ -122,6 +122,21 @@ def test_medium_plain_path_full_size(pkg, medium):
         r.close()
 
 
+def test_medium_without_duplicate_removal(pkg, medium):
+    """The join without duplicate removal (gsi_query_opts.no_dedup, the
+    bench's --no-dedup line) gives the same sets: ten medium queries, count
+    and full-set fingerprint against the oracle's."""
+    g, G, O, keys, labs = medium
+    qs = synth.queries("medium")
+    want = golden_counts("medium")
+    for i in range(0, len(qs), 10):
+        r = G.query(qs[i], no_dedup=True)
+        assert r.count == want[i]["count"], i
+        rows, s, x, _ = result_fingerprint(r, qs[i].k)
+        assert (rows, s, x) == tuple(int(v) for v in want[i]["fingerprint"]), i
+        r.close()
+
+
 def test_batched_prepared_batch_full_size(pkg, medium):
     g, G, O, keys, labs = medium
     qs = synth.queries("batched")
