@@ -27,8 +27,10 @@ gsi_result::~gsi_result() {
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
     cudaStream_t rs = own_stream ? stream : release_stream(device);
-    for (auto &c : chunks)
+    for (auto &c : chunks) {
         if (c.owned) cudaFreeAsync(c.rows, rs);
+        if (c.held) gsi::release_region(device, c.held);
+    }
     arena.reset();
     if (cur >= 0 && cur != device) cudaSetDevice(cur);
 }

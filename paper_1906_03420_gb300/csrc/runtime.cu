@@ -240,6 +240,37 @@ void Timer::resolve(gsi_stats *s) {
 // milliseconds per query; arenas up to tens of GB cost well under one.
 constexpr uint64_t DEVICE_ARENA_START = 16ull << 30;
 
+static std::atomic<uint64_t> g_total_mem[64];
+static std::atomic<uint64_t> g_held[64];
+
+uint64_t device_total_mem(int dev) {
+    if (dev < 0 || dev >= 64) return 0;
+    uint64_t t = g_total_mem[dev].load();
+    if (!t) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        t = tot;
+        g_total_mem[dev].store(t);
+    }
+    return t;
+}
+
+bool hold_region(int dev, uint64_t bytes) {
+    if (dev < 0 || dev >= 64) return false;
+    const uint64_t limit = device_total_mem(dev) / 4;
+    uint64_t cur = g_held[dev].load();
+    while (cur + bytes <= limit)
+        if (g_held[dev].compare_exchange_weak(cur, cur + bytes)) return true;
+    return false;
+}
+
+void release_region(int dev, uint64_t bytes) {
+    if (dev >= 0 && dev < 64) g_held[dev].fetch_sub(bytes);
+}
+
 static gsi_status dalloc(Exec &x, void **p, uint64_t bytes) {
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, x.st);
     if (e != cudaSuccess) {
@@ -483,6 +514,7 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
         if (cudaMemcpyAsync(h_pinned, &qc->fail, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(h_pinned + 1, &dst[k - 1].count, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(h_pinned + 2, &dst[k - 1].out_cap, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            (stats && cudaMemcpyAsync(h_pinned + 3, d_scalars + 1, 24, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             set_error("device-driven join: kernel or readback failed");
             rc = GSI_ECUDA;
@@ -490,6 +522,12 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
         fin[0] = h_pinned[0] & 0xffffffffu;
         fin[1] = h_pinned[1];
         fin[2] = h_pinned[2];
+        if (rc == GSI_OK && stats && fin[0] == 0) {   // the join's counters, read with the status
+            join_bytes = h_pinned[3];
+            join_items = h_pinned[4];
+            join_bytes_listwise = h_pinned[5];
+            stats_read = true;
+        }
     }
     if (rc == GSI_OK && (fin[0] & 4u)) {
         release();
@@ -514,8 +552,14 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     res->count += count;
     if (rows > 0) {
         const uint64_t bytes = rows * (uint64_t)k * 4;
-        if (bytes * 4 >= t_bytes) {
-            res->chunks.push_back({final_reg, rows});      // the result keeps the region
+        // the result keeps the region when its rows fill a quarter of it, or
+        // while the device's allowance for held regions lasts; otherwise the
+        // rows move to a tight buffer
+        const bool big = bytes * 4 >= t_bytes;
+        if (big || hold_region(g->device, t_bytes)) {
+            gsi_result::Chunk ch{final_reg, rows};
+            ch.held = big ? 0 : t_bytes;
+            res->chunks.push_back(ch);
             res->materialised += rows;
             reg[(k - 1) & 1] = nullptr;
         } else {
@@ -575,13 +619,10 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         // a fixed share of the device (not of the momentarily free memory, which
         // excludes blocks the stream-ordered pool keeps cached for reuse); the
         // device's total is looked up once
-        static std::atomic<uint64_t> total_mem[64];
-        uint64_t totm = g->device >= 0 && g->device < 64 ? total_mem[g->device].load() : 0;
+        const uint64_t totm = device_total_mem(g->device);
         if (!totm) {
-            size_t fr = 0, t2 = 0;
-            GSI_CUDA_TRY(cudaMemGetInfo(&fr, &t2));
-            totm = t2;
-            if (g->device >= 0 && g->device < 64) total_mem[g->device].store(totm);
+            set_error("query: device memory size unavailable");
+            return GSI_ECUDA;
         }
         x.budget = (uint64_t)(0.4 * (double)totm);
     }
@@ -732,7 +773,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
         }
         if (M0) cudaFreeAsync(M0, x.st);
     }
-    if (x.stats && rc == GSI_OK) {
+    if (x.stats && rc == GSI_OK && !(x.stats_read && !x.fell_back)) {
         // algorithmic bytes and candidates counted by the join kernels
         if (cudaMemcpyAsync(x.h_pinned, x.d_scalars + 1, 24, cudaMemcpyDeviceToHost, x.st) == cudaSuccess &&
             cudaStreamSynchronize(x.st) == cudaSuccess) {

@@ -26,6 +26,8 @@ struct gsi_result {
         int32_t *rows;       // device, row-major [nrows][k], column j = query vertex j
         uint64_t nrows;
         bool owned = true;   // false: the rows live in a shared arena
+        uint64_t held = 0;   // > 0: a whole table region kept without a tight copy,
+                             // counted against the device's held-region allowance
     };
     int32_t k = 0;
     int device = 0;
@@ -55,6 +57,15 @@ struct gsi_result {
     }
 
 namespace gsi {
+
+// Total memory of a device (looked up once per device).
+uint64_t device_total_mem(int dev);
+// Held table regions: a result may keep the whole region its rows were
+// written in (no tight copy) while the regions held on the device stay within
+// a quarter of its memory.  hold_region reserves `bytes` of that allowance
+// (false when it is used up); release_region returns it.
+bool hold_region(int dev, uint64_t bytes);
+void release_region(int dev, uint64_t bytes);
 
 struct QueryGraph {
     int32_t k = 0, qm = 0;
@@ -94,8 +105,9 @@ struct Exec {
     bool listwise = false;           // count whole-list bytes too (gsi_query_opts.listwise_bytes)
     bool nodedup = false;            // join without duplicate removal (gsi_query_opts.no_dedup)
     uint64_t join_bytes = 0, join_items = 0, join_bytes_listwise = 0;
-    uint64_t kernels = 0;
-    bool fell_back = false;          // the query ran host-driven            // kernels launched (scan = 3, partition, join, filter, seed = 3)
+    bool stats_read = false;         // the device path read the counters with its status
+    uint64_t kernels = 0;            // kernels launched (scan = 3, partition, join, filter, seed = 3)
+    bool fell_back = false;          // the query ran host-driven
     gsi_result *res = nullptr;
     gsi_stats *stats = nullptr;
     Timer tm;

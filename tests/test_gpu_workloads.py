@@ -122,6 +122,26 @@ def test_medium_plain_path_full_size(pkg, medium):
         r.close()
 
 
+def test_medium_results_kept_alive(pkg, medium):
+    """Results keep their table region while a quarter of the device's memory
+    allows, then move to tight copies: 24 results of the medium workload held
+    at once (more than that allowance holds), each one's count and full-set
+    fingerprint equal to the oracle's after all were made."""
+    g, G, O, keys, labs = medium
+    qs = synth.queries("medium")
+    want = golden_counts("medium")
+    small = sorted((i for i in range(len(qs)) if 0 < want[i]["count"] * qs[i].k * 4 < 1 << 30),
+                   key=lambda i: want[i]["count"])[:24]
+    assert len(small) == 24
+    held = [(i, G.query(qs[i])) for i in small]
+    for i, r in held:
+        assert r.count == want[i]["count"], i
+        rows, s, x, _ = result_fingerprint(r, qs[i].k)
+        assert (rows, s, x) == tuple(int(v) for v in want[i]["fingerprint"]), i
+    for _, r in held:
+        r.close()
+
+
 def test_medium_without_duplicate_removal(pkg, medium):
     """The join without duplicate removal (gsi_query_opts.no_dedup, the
     bench's --no-dedup line) gives the same sets: ten medium queries, count
