@@ -48,8 +48,6 @@ constexpr int SHORT_MAX = 16;     // rows with at most this many candidates are 
 // Rows of one slot tile of long rows: every long row spans at least
 // SHORT_MAX + 1 + W slots, plus a partial row at each end of the tile.
 constexpr int LONG_RMAX = JOIN_NV / (SHORT_MAX + 1 + JOIN_ROW_WEIGHT) + 2;
-constexpr int MEMO_EDGES = 4;     // linking edges of a step with a sub-list memo
-constexpr uint32_t MEMO_TAG_SHIFT = 59;
 
 // Rows whose bound exceeds SHORT_MAX, copied (t columns) with their bound
 // records, for the slot tiles.  count is a device counter.
@@ -99,32 +97,6 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint64_t bytes) {
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(x), "r"(chunk) : "memory");
         x += chunk;
     }
-}
-
-// Start (*lo) and length (returned) of the label(u) sub-list of N(v, lab[j]),
-// through the memo when the step has one.  A memo entry is
-// start | length << 32 | step << MEMO_TAG_SHIFT; concurrent writers store the
-// same value, and a load that sees an older entry (another step's, or a
-// stale cached line) only recomputes it.
-__device__ __forceinline__ uint32_t sublist(const JoinArgs &a, int j, int32_t v, uint32_t *lo) {
-    uint64_t *slot = nullptr;
-    if (a.memo && j < MEMO_EDGES) {
-        slot = a.memo + (uint64_t)j * (uint64_t)a.memo_n + (uint32_t)v;
-        const uint64_t e = *slot;
-        if ((uint32_t)(e >> MEMO_TAG_SHIFT) == (uint32_t)a.s.t) {
-            *lo = (uint32_t)e;
-            return (uint32_t)(e >> 32) & BOUND_LEN_MASK;
-        }
-    }
-    const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
-    const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
-    uint32_t l, h;
-    label_range(a.cl, x0, x1, (uint32_t)a.s.ulab, &l, &h);
-    *lo = l;
-    const uint32_t len = h - l;
-    if (slot && len <= BOUND_LEN_MASK)
-        *slot = (uint64_t)l | ((uint64_t)len << 32) | ((uint64_t)(uint32_t)a.s.t << MEMO_TAG_SHIFT);
-    return len;
 }
 
 // Length of the whole linking list N(v, lab[j]) (for the whole-list byte count).

@@ -177,6 +177,35 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
     return r;
 }
 
+constexpr int MEMO_EDGES = 4;     // linking edges of a step with a sub-list memo
+constexpr uint32_t MEMO_TAG_SHIFT = 59;
+
+// Start (*lo) and length (returned) of the label(u) sub-list of N(v, lab[j]),
+// through the memo when the step has one.  A memo entry is
+// start | length << 32 | step << MEMO_TAG_SHIFT; concurrent writers store the
+// same value, and a load that sees an older entry (another step's, or a
+// stale cached line) only recomputes it.
+__device__ __forceinline__ uint32_t sublist(const JoinArgs &a, int j, int32_t v, uint32_t *lo) {
+    uint64_t *slot = nullptr;
+    if (a.memo && j < MEMO_EDGES) {
+        slot = a.memo + (uint64_t)j * (uint64_t)a.memo_n + (uint32_t)v;
+        const uint64_t e = *slot;
+        if ((uint32_t)(e >> MEMO_TAG_SHIFT) == (uint32_t)a.s.t) {
+            *lo = (uint32_t)e;
+            return (uint32_t)(e >> 32) & BOUND_LEN_MASK;
+        }
+    }
+    const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+    const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
+    uint32_t l, h;
+    label_range(a.cl, x0, x1, (uint32_t)a.s.ulab, &l, &h);
+    *lo = l;
+    const uint32_t len = h - l;
+    if (slot && len <= BOUND_LEN_MASK)
+        *slot = (uint64_t)l | ((uint64_t)len << 32) | ((uint64_t)(uint32_t)a.s.t << MEMO_TAG_SHIFT);
+    return len;
+}
+
 // One tile of NV candidate slots.  The table-dependent inputs (M, R, F,
 // total, part, out, out_cap, out_count) are arguments so that the same code
 // serves host-sized launches (one CTA per tile) and device-sized persistent
@@ -188,8 +217,9 @@ __device__ inline int block_inclusive_max(int v, int *wt) {
 // With bounds (PRE: the long rows set aside by the row pass), each row's
 // shortest label sub-list is already known: bnd[r] holds its length and
 // linking-edge index (BOUND_LEN_BITS), blo[r] its start.  Staging then reads
-// those instead of searching, the other linking lists are probed whole with
-// the (label rank, id) key, and since every such row spans more than
+// those instead of searching, the other linking lists' label(u) sub-lists
+// come from the step's memo (filled by the row pass) or a label-range search,
+// and since every such row spans more than
 // SHORT_MAX + W slots a tile holds few rows, so each slot finds its row by a
 // binary search of the staged offsets instead of a block-wide scan.
 template <int NT, int VT, bool TILE_STATS = true, bool PRE = false>
@@ -233,8 +263,8 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         int32_t *rv = rowv + lr * t;
         for (int c = 0; c < t; ++c) rv[c] = __ldcg(row + c);
         if (PRE) {
-            // the bound scan's record: candidates from the shortest sub-list,
-            // every other linking list taken whole
+            // the bound scan's record: candidates from the shortest sub-list;
+            // every other linking list restricted to label(u)
             const uint32_t bw = __ldcg(bnd + r_lo + lr);
             const uint32_t best = bw & BOUND_LEN_MASK;
             const int jb = (int)(bw >> BOUND_LEN_BITS);
@@ -242,10 +272,10 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
             int q = 0;
             for (int j = 0; j < d && best > 0; ++j) {
                 if (j == jb) continue;
-                const uint64_t seg = (uint64_t)(uint32_t)rv[a.s.col[j]] * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
-                const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
-                lst[(lr * dm1 + q) * 2] = x0;
-                lst[(lr * dm1 + q) * 2 + 1] = x1 - x0;
+                uint32_t lo;
+                const uint32_t len = sublist(a, j, rv[a.s.col[j]], &lo);
+                lst[(lr * dm1 + q) * 2] = lo;
+                lst[(lr * dm1 + q) * 2 + 1] = len;
                 ++q;
             }
             continue;
@@ -301,16 +331,20 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
         __syncthreads();
     }
 
-    // ---- candidates: one slot per thread per round, consecutive slots per warp
+    // ---- candidates: one slot per thread per round, consecutive slots per
+    // warp; the VT slots' list loads, then their bitmap probes, are issued
+    // together
     int32_t wv[VT];
     int32_t lrv[VT];
-    unsigned okmask = 0;
+    uint32_t cix[VT];
+    unsigned okmask = 0, vmask = 0;
     unsigned long long items = 0;
 #pragma unroll
     for (int k = 0; k < VT; ++k) {
         const uint64_t s = s0 + (uint64_t)(k * NT + threadIdx.x);
         wv[k] = 0;
         lrv[k] = 0;
+        cix[k] = 0;
         if (s >= s1) continue;
         int lr;
         if (PRE) {
@@ -327,19 +361,28 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const int32_t *M, i
             lr = rowmap[s - s0];
         }
         const int64_t p = (int64_t)(s - Fs[lr]) - a.W;
+        lrv[k] = lr;
         if (p < 0) continue;            // a row-staging slot
         ++items;
-        const int32_t w = __ldg(a.ci + (uint64_t)base0[lr] + (uint64_t)p);
-        bool ok = (__ldg(a.cand + (w >> 5)) >> (w & 31)) & 1u;
-        const int32_t *rv = rowv + lr * t;
+        cix[k] = base0[lr] + (uint32_t)p;
+        vmask |= 1u << k;
+    }
+#pragma unroll
+    for (int k = 0; k < VT; ++k)
+        if ((vmask >> k) & 1u) wv[k] = __ldg(a.ci + cix[k]);
+    uint32_t bw[VT];
+#pragma unroll
+    for (int k = 0; k < VT; ++k) bw[k] = ((vmask >> k) & 1u) ? __ldg(a.cand + (wv[k] >> 5)) : 0u;
+#pragma unroll
+    for (int k = 0; k < VT; ++k) {
+        const int32_t w = wv[k];
+        bool ok = (bw[k] >> (w & 31)) & 1u;
+        const int32_t *rv = rowv + lrv[k] * t;
         for (uint32_t im = a.s.inj; ok && im; im &= im - 1) ok = rv[__ffs(im) - 1] != w;
         for (int j = 0; j < dm1 && ok; ++j) {
-            const uint32_t *ls = lst + (lr * dm1 + j) * 2;
-            if (PRE) ok = ranked_contains(a.ci, a.cl, ls[0], ls[0] + ls[1], (uint32_t)a.s.ulab, w);
-            else ok = sorted_contains(a.ci + ls[0], ls[1], w);
+            const uint32_t *ls = lst + (lrv[k] * dm1 + j) * 2;
+            ok = sorted_contains(a.ci + ls[0], ls[1], w);
         }
-        wv[k] = w;
-        lrv[k] = lr;
         if (ok) okmask |= 1u << k;
     }
 
