@@ -99,6 +99,32 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint64_t bytes) {
     }
 }
 
+// Copies n int32 from global src to shared dst (16-byte aligned) through L2
+// (the rows may have been written by other SMs), spread over NT threads: in
+// 16-byte pieces when src is 16-byte aligned, four pieces in flight per
+// thread; element by element otherwise.
+template <int NT>
+__device__ __forceinline__ void stage_rows(int32_t *dst, const int32_t *__restrict__ src, int n) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int nv = n >> 2;
+        const int4 *s4 = reinterpret_cast<const int4 *>(src);
+        int4 *d4 = reinterpret_cast<int4 *>(dst);
+        int i = threadIdx.x;
+        for (; i + 3 * NT < nv; i += 4 * NT) {
+            const int4 x0 = __ldcg(s4 + i), x1 = __ldcg(s4 + i + NT), x2 = __ldcg(s4 + i + 2 * NT),
+                       x3 = __ldcg(s4 + i + 3 * NT);
+            d4[i] = x0;
+            d4[i + NT] = x1;
+            d4[i + 2 * NT] = x2;
+            d4[i + 3 * NT] = x3;
+        }
+        for (; i < nv; i += NT) d4[i] = __ldcg(s4 + i);
+        for (int e = nv * 4 + threadIdx.x; e < n; e += NT) dst[e] = __ldcg(src + e);
+    } else {
+        for (int e = threadIdx.x; e < n; e += NT) dst[e] = __ldcg(src + e);
+    }
+}
+
 // Length of the whole linking list N(v, lab[j]) (for the whole-list byte count).
 __device__ __forceinline__ uint32_t whole_len(const JoinArgs &a, int j, int32_t v) {
     const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
@@ -295,11 +321,17 @@ __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_
         leader[q] = __ffs(peers) - 1;
         lead[q] = lane == leader[q] && lr < nb;
     }
-    // memo lookups of the group leaders
+    // memo lookups of the group leaders, with the list offsets beside them
+    // (used on a miss)
     uint64_t e[RPT];
+    uint32_t x0[RPT], x1[RPT];
 #pragma unroll
-    for (int q = 0; q < RPT; ++q)
+    for (int q = 0; q < RPT; ++q) {
         e[q] = (lead[q] && a.memo) ? a.memo[(uint32_t)v[q]] : 0ull;
+        const uint64_t seg = (uint64_t)(uint32_t)(lead[q] ? v[q] : 0) * (uint64_t)a.s.L + (uint64_t)a.s.lab[0];
+        x0[q] = lead[q] ? __ldg(a.off + seg) : 0u;
+        x1[q] = lead[q] ? __ldg(a.off + seg + 1) : 0u;
+    }
     uint32_t len[RPT], lo[RPT];
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
@@ -310,7 +342,12 @@ __device__ __forceinline__ void rows_join_single(const JoinArgs &a, const int32_
             lo[q] = (uint32_t)e[q];
             len[q] = (uint32_t)(e[q] >> 32) & BOUND_LEN_MASK;
         } else {
-            len[q] = sublist(a, 0, v[q], &lo[q]);
+            uint32_t h;
+            label_range(a.cl, x0[q], x1[q], (uint32_t)a.s.ulab, &lo[q], &h);
+            len[q] = h - lo[q];
+            if (a.memo && len[q] <= BOUND_LEN_MASK)
+                a.memo[(uint32_t)v[q]] = (uint64_t)lo[q] | ((uint64_t)len[q] << 32) |
+                                         ((uint64_t)(uint32_t)a.s.t << MEMO_TAG_SHIFT);
         }
     }
     // the first C candidates of every short group, then their bitmap probes
@@ -388,7 +425,7 @@ __device__ void row_pass(const JoinArgs &a, const int32_t *M, uint64_t R, uint64
         const int32_t *src = M + r0 * (uint64_t)t;
         if (threadIdx.x == 0 && r0 + stride < R)      // the next batch's rows, while this one runs
             prefetch_l2(M + (r0 + stride) * (uint64_t)t, min((uint64_t)NB, R - r0 - stride) * (uint64_t)t * 4);
-        for (int e = threadIdx.x; e < nb * t; e += NT) rowv[e] = __ldcg(src + e);
+        stage_rows<NT>(rowv, src, nb * t);
         __syncthreads();
         // this thread's rows q * NT + tid, q < RPT (a warp's lanes hold
         // consecutive rows)

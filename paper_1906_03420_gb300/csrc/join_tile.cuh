@@ -10,21 +10,24 @@ namespace gsi {
 // [lo, hi) of the entries with label rank `r` inside the (rank, id)-sorted list cl[a..b)
 __device__ inline void label_range(const uint16_t *__restrict__ cl, uint32_t a, uint32_t b, uint32_t r,
                                    uint32_t *lo, uint32_t *hi) {
-    uint32_t l = a, h = b;
-    while (l < h) {
-        uint32_t m = (l + h) >> 1;
-        if (__ldg(cl + m) < r) l = m + 1;
-        else h = m;
+    // the two bounds searched in lockstep: each round issues both probes,
+    // so the chain of dependent loads is as long as one search
+    uint32_t l1 = a, h1 = b, l2 = a, h2 = b;
+    while (l1 < h1 || l2 < h2) {
+        const uint32_t m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1;
+        const uint32_t c1 = l1 < h1 ? __ldg(cl + m1) : 0u;
+        const uint32_t c2 = l2 < h2 ? __ldg(cl + m2) : 0u;
+        if (l1 < h1) {
+            if (c1 < r) l1 = m1 + 1;
+            else h1 = m1;
+        }
+        if (l2 < h2) {
+            if (c2 <= r) l2 = m2 + 1;
+            else h2 = m2;
+        }
     }
-    const uint32_t s = l;
-    h = b;
-    while (l < h) {
-        uint32_t m = (l + h) >> 1;
-        if (__ldg(cl + m) <= r) l = m + 1;
-        else h = m;
-    }
-    *lo = s;
-    *hi = l;
+    *lo = l1;
+    *hi = l2;
 }
 
 struct StepDev {
@@ -187,16 +190,18 @@ constexpr uint32_t MEMO_TAG_SHIFT = 59;
 // stale cached line) only recomputes it.
 __device__ __forceinline__ uint32_t sublist(const JoinArgs &a, int j, int32_t v, uint32_t *lo) {
     uint64_t *slot = nullptr;
+    uint64_t e = 0;
+    const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
     if (a.memo && j < MEMO_EDGES) {
         slot = a.memo + (uint64_t)j * (uint64_t)a.memo_n + (uint32_t)v;
-        const uint64_t e = *slot;
-        if ((uint32_t)(e >> MEMO_TAG_SHIFT) == (uint32_t)a.s.t) {
-            *lo = (uint32_t)e;
-            return (uint32_t)(e >> 32) & BOUND_LEN_MASK;
-        }
+        e = *slot;
     }
-    const uint64_t seg = (uint64_t)(uint32_t)v * (uint64_t)a.s.L + (uint64_t)a.s.lab[j];
+    // the list's offsets are loaded beside the memo entry (used on a miss)
     const uint32_t x0 = __ldg(a.off + seg), x1 = __ldg(a.off + seg + 1);
+    if (slot && (uint32_t)(e >> MEMO_TAG_SHIFT) == (uint32_t)a.s.t) {
+        *lo = (uint32_t)e;
+        return (uint32_t)(e >> 32) & BOUND_LEN_MASK;
+    }
     uint32_t l, h;
     label_range(a.cl, x0, x1, (uint32_t)a.s.ulab, &l, &h);
     *lo = l;
