@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "embeddings/s & queries/s on 1 GB300; served p50/p99 vs plain per-query GPU path"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2: written between timed steps
-E2E_INFLIGHT = 4                    # results awaiting their host copy in the end-to-end loop
+E2E_INFLIGHT = 2                    # results awaiting their host copy in the end-to-end loop
 E2E_WARMUP = 2                      # untimed end-to-end passes before the timed ones
 
 
@@ -376,7 +376,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> dict | None:
                     r0, ev0 = inflight.popleft()
                     ev0.synchronize()
                     r0.close()
-                r = G.query(q, stream=stream, row_cap=row_cap)
+                r = G.query(q, stream=stream, row_cap=row_cap, tight_rows=True)
                 c = r.count
                 rows, _capped = r.copy_to_async(hosts[j % 2].data_ptr(), c, stream=copy_stream)
                 ev = _t.cuda.Event()

@@ -183,6 +183,13 @@ typedef struct {
                                 probes the bitmap alone (no warp groups, no
                                 sub-list memo); same results, for measuring
                                 what duplicate removal saves */
+    int32_t tight_rows;      /* 1: the final rows always move to a buffer of
+                                their own size and the table region they were
+                                written in is released at once (for callers
+                                that copy the rows out or keep many results);
+                                0: the result may keep the region (no copy)
+                                while held regions stay within a quarter of
+                                device memory */
 } gsi_query_opts;
 
 /*

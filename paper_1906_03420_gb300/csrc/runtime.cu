@@ -553,10 +553,10 @@ gsi_status Exec::run_device(uint64_t arena_bytes, bool *overflow, bool *no_memor
     if (rows > 0) {
         const uint64_t bytes = rows * (uint64_t)k * 4;
         // the result keeps the region when its rows fill a quarter of it, or
-        // while the device's allowance for held regions lasts; otherwise the
-        // rows move to a tight buffer
+        // while the device's allowance for held regions lasts; otherwise (and
+        // always when asked for tight rows) the rows move to a tight buffer
         const bool big = bytes * 4 >= t_bytes;
-        if (big || hold_region(g->device, t_bytes)) {
+        if (!tight_rows && (big || hold_region(g->device, t_bytes))) {
             gsi_result::Chunk ch{final_reg, rows};
             ch.held = big ? 0 : t_bytes;
             res->chunks.push_back(ch);
@@ -610,6 +610,7 @@ gsi_status run_query(gsi_graph *g, const QueryGraph &q, const gsi_query_opts &o,
     x.stats = o.stats;
     x.listwise = o.listwise_bytes != 0;
     x.nodedup = o.no_dedup != 0;
+    x.tight_rows = o.tight_rows != 0;
     x.res = res.get();
     x.tm.on = o.stats != nullptr;
     x.tm.st = x.st;

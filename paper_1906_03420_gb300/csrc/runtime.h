@@ -104,6 +104,7 @@ struct Exec {
     int count_only = 0;
     bool listwise = false;           // count whole-list bytes too (gsi_query_opts.listwise_bytes)
     bool nodedup = false;            // join without duplicate removal (gsi_query_opts.no_dedup)
+    bool tight_rows = false;         // final rows always to a tight buffer (gsi_query_opts.tight_rows)
     uint64_t join_bytes = 0, join_items = 0, join_bytes_listwise = 0;
     bool stats_read = false;         // the device path read the counters with its status
     uint64_t kernels = 0;            // kernels launched (scan = 3, partition, join, filter, seed = 3)

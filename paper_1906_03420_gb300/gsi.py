@@ -73,7 +73,8 @@ class c_query_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("row_cap", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64),
                 ("count_only", ctypes.c_int32), ("semantics", ctypes.c_int32),
                 ("order", ctypes.POINTER(ctypes.c_int32)), ("stats", ctypes.POINTER(c_stats)),
-                ("host_driven", ctypes.c_int32), ("listwise_bytes", ctypes.c_int32), ("no_dedup", ctypes.c_int32)]
+                ("host_driven", ctypes.c_int32), ("listwise_bytes", ctypes.c_int32), ("no_dedup", ctypes.c_int32),
+                ("tight_rows", ctypes.c_int32)]
 
 
 class c_query_desc(ctypes.Structure):
@@ -373,7 +374,7 @@ class Graph:
 
     def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
               order=None, stats: c_stats | None = None, host_driven: bool = False, semantics: int = 0,
-              listwise_bytes: bool = False, no_dedup: bool = False) -> Result:
+              listwise_bytes: bool = False, no_dedup: bool = False, tight_rows: bool = False) -> Result:
         qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
         o = c_query_opts()
         o.stream = _stream_handle(stream)
@@ -384,6 +385,7 @@ class Graph:
         o.host_driven = int(host_driven)
         o.listwise_bytes = int(listwise_bytes)
         o.no_dedup = int(no_dedup)
+        o.tight_rows = int(tight_rows)
         ordr = None
         if order is not None:
             ordr = _i32(order)
@@ -513,7 +515,7 @@ class EdgeGraph:
 
     def query(self, q, stream=None, row_cap: int = 0, mem_budget: int = 0, count_only: bool = False,
               order=None, stats: c_stats | None = None, host_driven: bool = False,
-              listwise_bytes: bool = False, no_dedup: bool = False) -> Result:
+              listwise_bytes: bool = False, no_dedup: bool = False, tight_rows: bool = False) -> Result:
         qa = q if isinstance(q, QueryArrays) else QueryArrays.of(q)
         o = c_query_opts()
         o.stream = _stream_handle(stream)
@@ -523,6 +525,7 @@ class EdgeGraph:
         o.host_driven = int(host_driven)
         o.listwise_bytes = int(listwise_bytes)
         o.no_dedup = int(no_dedup)
+        o.tight_rows = int(tight_rows)
         ordr = None
         if order is not None:
             ordr = _i32(order)

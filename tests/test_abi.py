@@ -160,7 +160,7 @@ def test_header_constants_match_the_binding(pkg):
     # every struct the binding passes by pointer has the header's field order and types
     fields = lambda name: [f[0] for f in getattr(b, name)._fields_]
     assert fields("c_query_opts") == ["stream", "row_cap", "mem_budget", "count_only", "semantics", "order", "stats",
-                                      "host_driven", "listwise_bytes", "no_dedup"]
+                                      "host_driven", "listwise_bytes", "no_dedup", "tight_rows"]
     assert fields("c_batch_opts") == ["stream", "row_cap", "mem_budget", "count_only", "stats", "seeds_per_item",
                                       "item_rows", "isect", "rows_per_thread", "block_threads"]
     assert fields("c_server_opts") == ["mem_budget", "n_streams", "row_cap", "count_only", "max_batch",

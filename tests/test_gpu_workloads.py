@@ -142,6 +142,21 @@ def test_medium_results_kept_alive(pkg, medium):
         r.close()
 
 
+def test_medium_tight_rows(pkg, medium):
+    """gsi_query_opts.tight_rows (the bench's end-to-end loop): the rows move
+    to a buffer of their own size, large results included; ten medium
+    queries, count and full-set fingerprint against the oracle's."""
+    g, G, O, keys, labs = medium
+    qs = synth.queries("medium")
+    want = golden_counts("medium")
+    for i in range(5, len(qs), 10):
+        r = G.query(qs[i], tight_rows=True)
+        assert r.count == want[i]["count"], i
+        rows, s, x, _ = result_fingerprint(r, qs[i].k)
+        assert (rows, s, x) == tuple(int(v) for v in want[i]["fingerprint"]), i
+        r.close()
+
+
 def test_medium_without_duplicate_removal(pkg, medium):
     """The join without duplicate removal (gsi_query_opts.no_dedup, the
     bench's --no-dedup line) gives the same sets: ten medium queries, count
