@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 METRIC = "embeddings/s & queries/s on 1 GB300; served p50/p99 vs plain per-query GPU path"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2: written between timed steps
 E2E_INFLIGHT = 2                    # results awaiting their host copy in the end-to-end loop
-E2E_WARMUP = 2                      # untimed end-to-end passes before the timed ones
+E2E_WARMUP = 4                      # untimed end-to-end passes before the timed ones
 
 
 def _threads() -> int:
